@@ -1,0 +1,740 @@
+/*
+ * oracle.c -- CPU oracle for enumerating weak pseudo-manifolds (Choi, Jang, Vallee,
+ * arXiv 2301.00806).
+ *
+ * TEST INFRASTRUCTURE ONLY. This is a plain, slow, deliberately unoptimised statement of
+ * what the GPU library computes. Only the tests, the smoke check and the bench's CPU
+ * baseline may build, load or call it. The GPU library shares no code with it: not its
+ * facet or ridge construction, its search, its bit layout or its sorting.
+ *
+ * What it computes (Section 2.1, Proposition 2.1): given candidate facets F_1..F_M
+ * (n-subsets of [m]) and affine properties g, the set of all K subset of F with every
+ * coordinate of A K in {0, 2} (A = ridge-facet incidence matrix) and g(K) > 0 for all g.
+ *
+ * Four independent routes to that set:
+ *   orc_enumerate_brute   the definition itself: every one of the 2^M subsets, in Gray
+ *                         order, checked by Proposition 2.1. M <= 40.
+ *   orc_enumerate_sweep   Section 2.1: every WPM lies in ker_Z2 A; a basis of that kernel
+ *                         is swept in Gray order and each combination K = BX is checked
+ *                         by Proposition 2.1 over Z.
+ *   orc_enumerate_dfs     the ridge-driven search (the canonical tree below), recursive,
+ *                         with plain byte arrays. It also reports node and probe counts.
+ *   orc_n2_cycle_sets     n = 2 only: a WPM of dimension 1 is a set of vertex-disjoint
+ *                         cycles of the candidate graph; counted by graph search.
+ *
+ * The canonical tree (the GPU search reproduces it node for node):
+ *   root: In = forced-in facets (plus facet {0..n-1} when the base facet is required),
+ *         Out = forced-out facets; the root dies if the two meet or a check below fails.
+ *   a node is a state (In, Out) that passed its checks. At a node:
+ *     - if some ridge has degree 1, take the lowest-index such ridge r. For each parent
+ *       p of r that is undecided (not in In, not in Out), in ascending index order, the
+ *       child is In + {p}, Out + (the other undecided parents of r).
+ *     - otherwise every ridge has degree 0 or 2 and In is a WPM (Proposition 2.1): it is
+ *       emitted when every g(In) > 0. Then, for each undecided facet f in ascending order,
+ *       the child is In + {f}, Out + (every undecided facet below f).
+ *   checks on a child (a rejected child is a "probe", an accepted one a "node"):
+ *     - adding the facet raises no ridge to degree 3;
+ *     - |In| <= cap (the upper-bound-theorem condition g = f - |K| + 1 > 0, Section 4.2);
+ *     - for each general affine g = c0 + sum c_j k_j: c0 + sum_{c_j>0} c_j
+ *       + sum_{j in In, c_j<0} c_j > 0 (an upper bound of g over every K containing In).
+ *   Node and probe counts are this tree's own quantities. The paper has no counterpart,
+ *   so they are "parity unpinned" against the paper; only the output set is pinned.
+ *
+ * Orders: facets and ridges are listed in lexicographic order of their sorted vertex
+ * tuples; output masks have facet j at bit j%64 of word j/64 and are sorted ascending as
+ * multiword unsigned integers (the highest word compared first).
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_ERR_INPUT -1
+#define ORC_ERR_CAPACITY -2
+#define ORC_ERR_NOMEM -5
+
+/* ---------------------------------------------------------------------------------- */
+/* GF(2) linear algebra on small vectors.                                             */
+/* ---------------------------------------------------------------------------------- */
+
+/* Rank over Z2 of k vectors given as bit masks: Gaussian elimination, one pivot bit at a
+ * time (the highest remaining bit of each kept vector). */
+static int gf2_rank_small(const uint32_t *v, int k)
+{
+    uint32_t basis[32];
+    int r = 0;
+    for (int i = 0; i < k; i++) {
+        uint32_t x = v[i];
+        /* reduce x by the basis, pivoting on each basis vector's highest bit */
+        for (int j = 0; j < r; j++) {
+            int hb = 31 - __builtin_clz(basis[j]);
+            if ((x >> hb) & 1u) x ^= basis[j];
+        }
+        if (x) {
+            /* keep the basis in a form where every pivot bit appears in one vector only */
+            int hb = 31 - __builtin_clz(x);
+            for (int j = 0; j < r; j++)
+                if ((basis[j] >> hb) & 1u) basis[j] ^= x;
+            basis[r++] = x;
+        }
+    }
+    return r;
+}
+
+/* ---------------------------------------------------------------------------------- */
+/* Candidate facets (Section 3.1 non-singularity; Section 4.2, Proposition 4.2).      */
+/* ---------------------------------------------------------------------------------- */
+
+/* Advance c[0..k-1] (strictly increasing, values < m) to the next k-subset in
+ * lexicographic order. Returns 0 when the last subset has been passed. */
+static int next_combination(int *c, int k, int m)
+{
+    int i = k - 1;
+    while (i >= 0 && c[i] == m - k + i) i--;
+    if (i < 0) return 0;
+    c[i]++;
+    for (int j = i + 1; j < k; j++) c[j] = c[j - 1] + 1;
+    return 1;
+}
+
+/*
+ * The candidate facets of a mod-2 characteristic map, in lexicographic order.
+ *  kind 0 (primal): cols[i] is lambda(i) in Z2^n. An n-subset sigma is a candidate when
+ *                   {lambda(i) : i in sigma} is linearly independent, i.e. a basis of Z2^n
+ *                   (the non-singularity condition, Section 3.1).
+ *  kind 1 (dual):   cols[i] is the dual row lambda-bar(i) in Z2^(m-n). By linear Gale
+ *                   duality (Proposition 4.2) sigma is a candidate when the rows indexed
+ *                   by the complement [m] \ sigma form a basis of Z2^(m-n).
+ * Writes vertex masks (bit i = vertex i) to facets[0..]; returns M, or a negative error.
+ */
+int orc_candidate_facets(int kind, int n, int m, const uint32_t *cols, uint16_t *facets, int cap)
+{
+    if (n < 1 || m < n || m > 16 || (kind != 0 && kind != 1)) return ORC_ERR_INPUT;
+    int c[16];
+    for (int i = 0; i < n; i++) c[i] = i;
+    int M = 0;
+    do {
+        uint32_t v[16];
+        int k = 0, need;
+        int in_sigma[16] = {0};
+        for (int i = 0; i < n; i++) in_sigma[c[i]] = 1;
+        if (kind == 0) {
+            for (int i = 0; i < n; i++) v[k++] = cols[c[i]];
+            need = n;
+        } else {
+            for (int i = 0; i < m; i++)
+                if (!in_sigma[i]) v[k++] = cols[i];
+            need = m - n;
+        }
+        if (gf2_rank_small(v, k) == need) {
+            if (M >= cap) return ORC_ERR_CAPACITY;
+            uint16_t mask = 0;
+            for (int i = 0; i < n; i++) mask |= (uint16_t)(1u << c[i]);
+            facets[M++] = mask;
+        }
+    } while (next_combination(c, n, m));
+    return M;
+}
+
+/* ---------------------------------------------------------------------------------- */
+/* Ridges and the ridge-facet incidence (Section 2.1).                                */
+/* ---------------------------------------------------------------------------------- */
+
+typedef struct {
+    int n, M, N;
+    uint16_t *ridge;   /* [N] vertex masks, lexicographic order                         */
+    int *npar;         /* [N] number of parents P(r)                                     */
+    int *par;          /* [N * M] parents of r, ascending (row r holds npar[r] entries)  */
+    int *fr;           /* [M * n] the n ridges of each facet, by ridge index              */
+} incidence_t;
+
+static void incidence_free(incidence_t *I)
+{
+    free(I->ridge); free(I->npar); free(I->par); free(I->fr);
+    memset(I, 0, sizeof(*I));
+}
+
+/* The ridges are every (n-1)-subset of [m] that lies in at least one candidate facet,
+ * found by walking all (n-1)-subsets in lexicographic order and testing containment
+ * against every facet. The parents of r are the facets that contain it. */
+static int incidence_build(int n, int M, const uint16_t *facets, incidence_t *I)
+{
+    memset(I, 0, sizeof(*I));
+    I->n = n; I->M = M;
+    if (n < 2 || M < 0) return ORC_ERR_INPUT;
+    uint16_t all = 0;
+    for (int j = 0; j < M; j++) all |= facets[j];
+    int m = 0;
+    while (m < 16 && (all >> m)) m++;
+    if (m < n) m = n;
+    /* upper bound on the number of ridges: C(m, n-1) */
+    long cap = 1;
+    for (int i = 0; i < n - 1; i++) cap = cap * (m - i) / (i + 1);
+    I->ridge = (uint16_t *)malloc(sizeof(uint16_t) * (cap ? cap : 1));
+    I->npar = (int *)calloc(cap ? cap : 1, sizeof(int));
+    I->par = (int *)malloc(sizeof(int) * (size_t)(cap ? cap : 1) * (M ? M : 1));
+    I->fr = (int *)malloc(sizeof(int) * (size_t)(M ? M : 1) * n);
+    if (!I->ridge || !I->npar || !I->par || !I->fr) { incidence_free(I); return ORC_ERR_NOMEM; }
+    int c[16];
+    for (int i = 0; i < n - 1; i++) c[i] = i;
+    int N = 0;
+    do {
+        uint16_t r = 0;
+        for (int i = 0; i < n - 1; i++) r |= (uint16_t)(1u << c[i]);
+        int np = 0;
+        for (int j = 0; j < M; j++)
+            if ((facets[j] & r) == r) I->par[(size_t)N * M + np++] = j;
+        if (np > 0) {
+            I->ridge[N] = r;
+            I->npar[N] = np;
+            N++;
+        }
+    } while (n - 1 > 0 && next_combination(c, n - 1, m));
+    I->N = N;
+    for (int j = 0; j < M; j++) {
+        int k = 0;
+        for (int r = 0; r < N; r++)
+            if ((facets[j] & I->ridge[r]) == I->ridge[r]) I->fr[j * n + k++] = r;
+        if (k != n) { incidence_free(I); return ORC_ERR_INPUT; } /* facet of wrong size */
+    }
+    return ORC_OK;
+}
+
+/* Ridges (vertex masks, lexicographic order) and parent counts, for tests. */
+int orc_ridges(int n, int M, const uint16_t *facets, uint16_t *ridges, int32_t *npar, int cap)
+{
+    incidence_t I;
+    int rc = incidence_build(n, M, facets, &I);
+    if (rc) return rc;
+    int N = I.N;
+    if (N > cap) { incidence_free(&I); return ORC_ERR_CAPACITY; }
+    for (int r = 0; r < N; r++) { ridges[r] = I.ridge[r]; npar[r] = I.npar[r]; }
+    incidence_free(&I);
+    return N;
+}
+
+/* dim ker_Z2 A = M - rank_Z2(A), A the N x M ridge-facet incidence matrix (Section 2.1).
+ * Rank by Gaussian elimination over the rows of A stored as M-bit rows. */
+static int gf2_kernel_basis(const incidence_t *I, uint64_t **basis_out, int *s_out)
+{
+    int M = I->M, N = I->N;
+    int W = (M + 63) / 64;
+    uint64_t *rows = (uint64_t *)calloc((size_t)(N ? N : 1) * W, sizeof(uint64_t));
+    int *pivcol = (int *)malloc(sizeof(int) * (N ? N : 1));
+    char *is_pivot = (char *)calloc(M ? M : 1, 1);
+    if (!rows || !pivcol || !is_pivot) { free(rows); free(pivcol); free(is_pivot); return ORC_ERR_NOMEM; }
+    for (int r = 0; r < N; r++)
+        for (int k = 0; k < I->npar[r]; k++) {
+            int j = I->par[(size_t)r * M + k];
+            rows[(size_t)r * W + j / 64] |= 1ull << (j % 64);
+        }
+    /* reduced row echelon form */
+    int rank = 0;
+    for (int col = 0; col < M && rank < N; col++) {
+        int sel = -1;
+        for (int r = rank; r < N; r++)
+            if ((rows[(size_t)r * W + col / 64] >> (col % 64)) & 1ull) { sel = r; break; }
+        if (sel < 0) continue;
+        if (sel != rank)
+            for (int w = 0; w < W; w++) {
+                uint64_t t = rows[(size_t)sel * W + w];
+                rows[(size_t)sel * W + w] = rows[(size_t)rank * W + w];
+                rows[(size_t)rank * W + w] = t;
+            }
+        for (int r = 0; r < N; r++)
+            if (r != rank && ((rows[(size_t)r * W + col / 64] >> (col % 64)) & 1ull))
+                for (int w = 0; w < W; w++) rows[(size_t)r * W + w] ^= rows[(size_t)rank * W + w];
+        pivcol[rank] = col;
+        is_pivot[col] = 1;
+        rank++;
+    }
+    int s = M - rank;
+    if (basis_out) {
+        /* one kernel vector per free column f: x_f = 1, x_pivot(r) = row r's bit at f */
+        uint64_t *B = (uint64_t *)calloc((size_t)(s ? s : 1) * W, sizeof(uint64_t));
+        if (!B) { free(rows); free(pivcol); free(is_pivot); return ORC_ERR_NOMEM; }
+        int t = 0;
+        for (int f = 0; f < M; f++) {
+            if (is_pivot[f]) continue;
+            B[(size_t)t * W + f / 64] |= 1ull << (f % 64);
+            for (int r = 0; r < rank; r++)
+                if ((rows[(size_t)r * W + f / 64] >> (f % 64)) & 1ull)
+                    B[(size_t)t * W + pivcol[r] / 64] |= 1ull << (pivcol[r] % 64);
+            t++;
+        }
+        *basis_out = B;
+    }
+    free(rows); free(pivcol); free(is_pivot);
+    *s_out = s;
+    return ORC_OK;
+}
+
+int orc_kernel_dim(int n, int M, const uint16_t *facets)
+{
+    incidence_t I;
+    int rc = incidence_build(n, M, facets, &I);
+    if (rc) return rc;
+    int s = 0;
+    rc = gf2_kernel_basis(&I, NULL, &s);
+    incidence_free(&I);
+    return rc ? rc : s;
+}
+
+/* ---------------------------------------------------------------------------------- */
+/* Conditions (Section 2.1 properties; Section 4.2 upper bound; Section 4.4 forced).  */
+/* ---------------------------------------------------------------------------------- */
+
+typedef struct {
+    int32_t cap;                /* |K| <= cap; -1: none; -2: the Section 4.2 bound for n */
+    int32_t base_facet;         /* nonzero: facet {0..n-1} must be in K (Section 3.1)     */
+    const uint64_t *forced_in;  /* NULL or ceil(M/64) words: facets that must be in K     */
+    const uint64_t *forced_out; /* NULL or ceil(M/64) words: facets that must not be in K */
+    int32_t n_affine;           /* general properties g(K) = c0 + sum_j c_j k_j > 0      */
+    const int32_t *c0;          /* [n_affine]                                             */
+    const int32_t *coef;        /* [n_affine * M]                                         */
+} orc_cond;
+
+typedef struct {
+    uint64_t count, nodes, probes;
+} orc_stats;
+
+static long binom(int a, int b)
+{
+    if (b < 0 || a < b) return 0;
+    long r = 1;
+    for (int i = 0; i < b; i++) r = r * (a - i) / (i + 1);
+    return r;
+}
+
+/* f_{n-1}(C^n(n+4)) = C(n+4-ceil(n/2), 4) + C(n+3-floor(n/2), 4)  (Section 4.2). */
+int orc_ubt_cap(int n)
+{
+    return (int)(binom(n + 4 - (n + 1) / 2, 4) + binom(n + 3 - n / 2, 4));
+}
+
+/* Resolve the cap: -2 means the Section 4.2 bound, which is stated for m = n + 4. */
+static int resolve_cap(int cap, int n, int m)
+{
+    if (cap == -2) return (m == n + 4) ? orc_ubt_cap(n) : -3;
+    return cap;
+}
+
+/* The base facet {0..n-1} as a candidate index, or -1 when it is not a candidate. */
+static int base_facet_index(int n, int M, const uint16_t *facets)
+{
+    uint16_t b = (uint16_t)((1u << n) - 1u);
+    for (int j = 0; j < M; j++)
+        if (facets[j] == b) return j;
+    return -1;
+}
+
+static int bit_of(const uint64_t *w, int j) { return (int)((w[j / 64] >> (j % 64)) & 1ull); }
+
+/* Every g(K) > 0 for K given as a 0/1 array, computed from the definition. */
+static int affine_ok(const orc_cond *c, int M, const char *inK)
+{
+    for (int a = 0; a < c->n_affine; a++) {
+        long g = c->c0[a];
+        for (int j = 0; j < M; j++)
+            if (inK[j]) g += c->coef[(size_t)a * M + j];
+        if (g <= 0) return 0;
+    }
+    return 1;
+}
+
+/* ---------------------------------------------------------------------------------- */
+/* Output collection.                                                                 */
+/* ---------------------------------------------------------------------------------- */
+
+typedef struct {
+    uint64_t *masks;   /* caller buffer, cap * W words, or NULL for counting only */
+    uint64_t cap;
+    uint64_t count;
+    int W;
+    int overflow;
+} sink_t;
+
+static void sink_emit(sink_t *s, int M, const char *inK)
+{
+    if (s->masks) {
+        if (s->count < s->cap) {
+            uint64_t *dst = s->masks + s->count * (uint64_t)s->W;
+            memset(dst, 0, sizeof(uint64_t) * s->W);
+            for (int j = 0; j < M; j++)
+                if (inK[j]) dst[j / 64] |= 1ull << (j % 64);
+        } else {
+            s->overflow = 1;
+        }
+    }
+    s->count++;
+}
+
+static int g_sort_W;
+static int cmp_masks(const void *pa, const void *pb)
+{
+    const uint64_t *a = (const uint64_t *)pa, *b = (const uint64_t *)pb;
+    for (int w = g_sort_W - 1; w >= 0; w--) {
+        if (a[w] < b[w]) return -1;
+        if (a[w] > b[w]) return 1;
+    }
+    return 0;
+}
+
+static int sink_finish(sink_t *s)
+{
+    if (s->masks && !s->overflow) {
+        g_sort_W = s->W;
+        qsort(s->masks, s->count, sizeof(uint64_t) * s->W, cmp_masks);
+    }
+    return s->overflow ? ORC_ERR_CAPACITY : ORC_OK;
+}
+
+/* ---------------------------------------------------------------------------------- */
+/* O3: the definition. Every subset K of the M candidates, visited in Gray-code order */
+/* (one facet toggled per step), keeping the ridge degrees of A K up to date.         */
+/* ---------------------------------------------------------------------------------- */
+
+int orc_enumerate_brute(int n, int m, int M, const uint16_t *facets, const orc_cond *c,
+                        uint64_t *masks, uint64_t cap_masks, orc_stats *st)
+{
+    if (M > 40) return ORC_ERR_INPUT;
+    int cap = resolve_cap(c->cap, n, m);
+    if (cap == -3) return ORC_ERR_INPUT;
+    incidence_t I;
+    int rc = incidence_build(n, M, facets, &I);
+    if (rc) return rc;
+    int base = c->base_facet ? base_facet_index(n, M, facets) : -1;
+    sink_t s = { masks, cap_masks, 0, (M + 63) / 64, 0 };
+    int *deg = (int *)calloc(I.N ? I.N : 1, sizeof(int));
+    char *inK = (char *)calloc(M ? M : 1, 1);
+    int bad = 0;     /* ridges whose degree is not 0 or 2 */
+    int size = 0;
+    int fin_need = 0, fin_have = 0, fout_have = 0;
+    for (int j = 0; j < M; j++) {
+        int fi = (c->forced_in && bit_of(c->forced_in, j)) || j == base;
+        fin_need += fi;
+    }
+    if (c->base_facet && base < 0) fin_need = -1; /* never satisfiable */
+    uint64_t total = (M == 64) ? 0 : (1ull << M);
+    for (uint64_t i = 0;; i++) {
+        if (i > 0) {
+            if (i == total) break;
+            int j = __builtin_ctzll(i);
+            int delta = inK[j] ? -1 : 1;
+            inK[j] = (char)!inK[j];
+            size += delta;
+            if ((c->forced_in && bit_of(c->forced_in, j)) || j == base) fin_have += delta;
+            if (c->forced_out && bit_of(c->forced_out, j)) fout_have += delta;
+            for (int k = 0; k < n; k++) {
+                int r = I.fr[j * n + k];
+                int before_ok = (deg[r] == 0 || deg[r] == 2);
+                deg[r] += delta;
+                int after_ok = (deg[r] == 0 || deg[r] == 2);
+                bad += before_ok - after_ok;
+            }
+        }
+        if (bad == 0 && fin_have == fin_need && fout_have == 0 && (cap < 0 || size <= cap) &&
+            affine_ok(c, M, inK))
+            sink_emit(&s, M, inK);
+    }
+    free(deg); free(inK);
+    incidence_free(&I);
+    rc = sink_finish(&s);
+    if (st) { st->count = s.count; st->nodes = 0; st->probes = 0; }
+    return rc;
+}
+
+/* ---------------------------------------------------------------------------------- */
+/* O2: Section 2.1. Sweep all 2^s elements K = BX of ker_Z2 A (Gray order over X) and */
+/* keep those whose degrees A K over Z are all in {0, 2} (Proposition 2.1).           */
+/* ---------------------------------------------------------------------------------- */
+
+int orc_enumerate_sweep(int n, int m, int M, const uint16_t *facets, const orc_cond *c,
+                        uint64_t *masks, uint64_t cap_masks, orc_stats *st, int max_s)
+{
+    int cap = resolve_cap(c->cap, n, m);
+    if (cap == -3) return ORC_ERR_INPUT;
+    incidence_t I;
+    int rc = incidence_build(n, M, facets, &I);
+    if (rc) return rc;
+    uint64_t *B = NULL;
+    int s = 0;
+    rc = gf2_kernel_basis(&I, &B, &s);
+    if (rc) { incidence_free(&I); return rc; }
+    if (s > max_s || s > 62) { free(B); incidence_free(&I); return ORC_ERR_INPUT; }
+    int W = (M + 63) / 64;
+    int base = c->base_facet ? base_facet_index(n, M, facets) : -1;
+    sink_t snk = { masks, cap_masks, 0, W, 0 };
+    int *deg = (int *)calloc(I.N ? I.N : 1, sizeof(int));
+    char *inK = (char *)calloc(M ? M : 1, 1);
+    int bad = 0;   /* ridges of degree not in {0, 2}: in the kernel, the degree-4 ones */
+    int size = 0;
+    for (uint64_t i = 0; i < (1ull << s); i++) {
+        if (i > 0) {
+            int t = __builtin_ctzll(i);
+            for (int j = 0; j < M; j++) {
+                if (!((B[(size_t)t * W + j / 64] >> (j % 64)) & 1ull)) continue;
+                int delta = inK[j] ? -1 : 1;
+                inK[j] = (char)!inK[j];
+                size += delta;
+                for (int k = 0; k < n; k++) {
+                    int r = I.fr[j * n + k];
+                    int before_ok = (deg[r] == 0 || deg[r] == 2);
+                    deg[r] += delta;
+                    int after_ok = (deg[r] == 0 || deg[r] == 2);
+                    bad += before_ok - after_ok;
+                }
+            }
+        }
+        if (bad) continue;
+        if (cap >= 0 && size > cap) continue;
+        if (c->base_facet && (base < 0 || !inK[base])) continue;
+        int ok = 1;
+        for (int j = 0; j < M && ok; j++) {
+            if (c->forced_in && bit_of(c->forced_in, j) && !inK[j]) ok = 0;
+            if (c->forced_out && bit_of(c->forced_out, j) && inK[j]) ok = 0;
+        }
+        if (ok && affine_ok(c, M, inK)) sink_emit(&snk, M, inK);
+    }
+    free(deg); free(inK); free(B);
+    incidence_free(&I);
+    rc = sink_finish(&snk);
+    if (st) { st->count = snk.count; st->nodes = 0; st->probes = 0; }
+    return rc;
+}
+
+/* ---------------------------------------------------------------------------------- */
+/* O1: the ridge-driven search, the canonical tree described at the top of the file.  */
+/* ---------------------------------------------------------------------------------- */
+
+enum { UNDECIDED = 0, IN = 1, OUT = 2 };
+
+typedef struct {
+    const incidence_t *I;
+    const orc_cond *c;
+    int cap;
+    long *posall;          /* [n_affine]: sum of the positive coefficients            */
+    long *negin;           /* [n_affine]: sum of the negative coefficients over In    */
+    unsigned char *deg;    /* [N] ridge degrees (A K)_r                               */
+    char *st;              /* [M] UNDECIDED / IN / OUT                                */
+    char *inK;             /* [M] 1 when the facet is in In                           */
+    int size;              /* |In|                                                    */
+    sink_t *sink;
+    uint64_t nodes, probes;
+} dfs_t;
+
+/* Try to add facet p to In. Returns 1 and applies it when every check of the canonical
+ * tree passes; returns 0 and changes nothing otherwise. */
+static int dfs_add(dfs_t *d, int p)
+{
+    const incidence_t *I = d->I;
+    int n = I->n, M = I->M;
+    for (int k = 0; k < n; k++)
+        if (d->deg[I->fr[p * n + k]] >= 2) return 0;          /* degree would reach 3 */
+    if (d->cap >= 0 && d->size + 1 > d->cap) return 0;       /* upper bound on |K|   */
+    for (int a = 0; a < d->c->n_affine; a++) {
+        long cp = d->c->coef[(size_t)a * M + p];
+        long bound = d->c->c0[a] + d->posall[a] + d->negin[a] + (cp < 0 ? cp : 0);
+        if (bound <= 0) return 0;                             /* no completion has g > 0 */
+    }
+    for (int k = 0; k < n; k++) d->deg[I->fr[p * n + k]]++;
+    for (int a = 0; a < d->c->n_affine; a++) {
+        long cp = d->c->coef[(size_t)a * M + p];
+        if (cp < 0) d->negin[a] += cp;
+    }
+    d->st[p] = IN;
+    d->inK[p] = 1;
+    d->size++;
+    return 1;
+}
+
+static void dfs_remove(dfs_t *d, int p)
+{
+    const incidence_t *I = d->I;
+    int n = I->n, M = I->M;
+    for (int k = 0; k < n; k++) d->deg[I->fr[p * n + k]]--;
+    for (int a = 0; a < d->c->n_affine; a++) {
+        long cp = d->c->coef[(size_t)a * M + p];
+        if (cp < 0) d->negin[a] -= cp;
+    }
+    d->st[p] = UNDECIDED;
+    d->inK[p] = 0;
+    d->size--;
+}
+
+static void dfs_visit(dfs_t *d)
+{
+    const incidence_t *I = d->I;
+    int M = I->M, N = I->N;
+    d->nodes++;
+    int r = -1;
+    for (int i = 0; i < N; i++)
+        if (d->deg[i] == 1) { r = i; break; }
+    if (r >= 0) {
+        /* ridge branch: exactly one more parent of r must join */
+        int np = I->npar[r];
+        const int *par = I->par + (size_t)r * M;
+        int und[64], nu = 0;
+        for (int k = 0; k < np; k++)
+            if (d->st[par[k]] == UNDECIDED) und[nu++] = par[k];
+        for (int a = 0; a < nu; a++) {
+            int p = und[a];
+            for (int b = 0; b < nu; b++)
+                if (b != a) d->st[und[b]] = OUT;
+            if (dfs_add(d, p)) {
+                dfs_visit(d);
+                dfs_remove(d, p);
+            } else {
+                d->probes++;
+            }
+            for (int b = 0; b < nu; b++)
+                if (b != a) d->st[und[b]] = UNDECIDED;
+        }
+        return;
+    }
+    /* closure: In is a weak pseudo-manifold (Proposition 2.1) */
+    if (affine_ok(d->c, M, d->inK)) sink_emit(d->sink, M, d->inK);
+    int *und = (int *)malloc(sizeof(int) * (M ? M : 1));
+    int nu = 0;
+    for (int f = 0; f < M; f++)
+        if (d->st[f] == UNDECIDED) und[nu++] = f;
+    for (int a = 0; a < nu; a++) {
+        int f = und[a];
+        for (int b = 0; b < a; b++) d->st[und[b]] = OUT;
+        if (dfs_add(d, f)) {
+            dfs_visit(d);
+            dfs_remove(d, f);
+        } else {
+            d->probes++;
+        }
+        for (int b = 0; b < a; b++) d->st[und[b]] = UNDECIDED;
+    }
+    free(und);
+}
+
+int orc_enumerate_dfs(int n, int m, int M, const uint16_t *facets, const orc_cond *c,
+                      uint64_t *masks, uint64_t cap_masks, orc_stats *st)
+{
+    int cap = resolve_cap(c->cap, n, m);
+    if (cap == -3) return ORC_ERR_INPUT;
+    incidence_t I;
+    int rc = incidence_build(n, M, facets, &I);
+    if (rc) return rc;
+    sink_t snk = { masks, cap_masks, 0, (M + 63) / 64, 0 };
+    dfs_t d;
+    memset(&d, 0, sizeof(d));
+    d.I = &I; d.c = c; d.cap = cap; d.sink = &snk;
+    int na = c->n_affine;
+    d.posall = (long *)calloc(na ? na : 1, sizeof(long));
+    d.negin = (long *)calloc(na ? na : 1, sizeof(long));
+    d.deg = (unsigned char *)calloc(I.N ? I.N : 1, 1);
+    d.st = (char *)calloc(M ? M : 1, 1);
+    d.inK = (char *)calloc(M ? M : 1, 1);
+    for (int a = 0; a < na; a++)
+        for (int j = 0; j < M; j++) {
+            long cj = c->coef[(size_t)a * M + j];
+            if (cj > 0) d.posall[a] += cj;
+        }
+    /* the root: forced-in facets (and the base facet) in, forced-out facets out */
+    int root_ok = 1;
+    int base = c->base_facet ? base_facet_index(n, M, facets) : -1;
+    if (c->base_facet && base < 0) root_ok = 0;
+    for (int j = 0; j < M && root_ok; j++)
+        if (c->forced_out && bit_of(c->forced_out, j)) {
+            if ((c->forced_in && bit_of(c->forced_in, j)) || j == base) root_ok = 0;
+            d.st[j] = OUT;
+        }
+    for (int j = 0; j < M && root_ok; j++)
+        if ((c->forced_in && bit_of(c->forced_in, j)) || j == base)
+            if (!dfs_add(&d, j)) root_ok = 0;
+    if (root_ok)
+        dfs_visit(&d);
+    else
+        d.probes++;
+    free(d.posall); free(d.negin); free(d.deg); free(d.st); free(d.inK);
+    incidence_free(&I);
+    rc = sink_finish(&snk);
+    if (st) { st->count = snk.count; st->nodes = d.nodes; st->probes = d.probes; }
+    return rc;
+}
+
+/* ---------------------------------------------------------------------------------- */
+/* O4: n = 2. A pure 1-dimensional complex is a graph; it is a WPM exactly when every  */
+/* vertex (ridge) has degree 0 or 2, i.e. it is a set of vertex-disjoint cycles.      */
+/* Count those sets (with at most max_edges edges in total; -1 for no limit) by        */
+/* listing every simple cycle of the candidate graph, then every family of pairwise   */
+/* vertex-disjoint cycles.                                                             */
+/* ---------------------------------------------------------------------------------- */
+
+typedef struct { uint16_t verts; int len; } cycle_t;
+
+static int adj_has(const uint16_t *adj, int a, int b) { return (adj[a] >> b) & 1; }
+
+static void cycles_from(const uint16_t *adj, int s, int v, uint16_t used, int len, int second,
+                        cycle_t *out, int *nout, int cap)
+{
+    for (int w = s + 1; w < 16; w++) {
+        if (!adj_has(adj, v, w) || ((used >> w) & 1)) continue;
+        cycles_from(adj, s, w, used | (uint16_t)(1u << w), len + 1, len == 1 ? w : second,
+                    out, nout, cap);
+    }
+    /* close the path v -> s: a cycle needs 3+ vertices; keep one of its two directions
+     * (the one whose second vertex is below its last vertex) */
+    if (len >= 3 && adj_has(adj, v, s) && second < v) {
+        if (*nout < cap) { out[*nout].verts = used; out[*nout].len = len; }
+        (*nout)++;
+    }
+}
+
+static long count_families(const cycle_t *cy, int nc, int from, uint16_t used, int edges,
+                           int max_edges)
+{
+    long total = 1; /* the family chosen so far */
+    for (int i = from; i < nc; i++) {
+        if (cy[i].verts & used) continue;
+        if (max_edges >= 0 && edges + cy[i].len > max_edges) continue;
+        total += count_families(cy, nc, i + 1, used | cy[i].verts, edges + cy[i].len, max_edges);
+    }
+    return total;
+}
+
+/* edges: M vertex masks with two bits each. Returns the number of WPMs, or < 0. */
+long orc_n2_cycle_sets(int M, const uint16_t *edges, int max_edges)
+{
+    uint16_t adj[16] = {0};
+    for (int j = 0; j < M; j++) {
+        if (__builtin_popcount(edges[j]) != 2) return ORC_ERR_INPUT;
+        int a = __builtin_ctz(edges[j]);
+        int b = 15 - __builtin_clz((unsigned)edges[j] << 16);
+        adj[a] |= (uint16_t)(1u << b);
+        adj[b] |= (uint16_t)(1u << a);
+    }
+    int cap = 1 << 16;
+    cycle_t *cy = (cycle_t *)malloc(sizeof(cycle_t) * cap);
+    int nc = 0;
+    for (int s = 0; s < 16; s++)
+        cycles_from(adj, s, s, (uint16_t)(1u << s), 1, -1, cy, &nc, cap);
+    if (nc > cap) { free(cy); return ORC_ERR_CAPACITY; }
+    long total = count_families(cy, nc, 0, 0, 0, max_edges);
+    free(cy);
+    return total;
+}
+
+/* Number of simple cycles of the candidate graph (n = 2), for tests. */
+long orc_n2_cycle_count(int M, const uint16_t *edges)
+{
+    uint16_t adj[16] = {0};
+    for (int j = 0; j < M; j++) {
+        int a = __builtin_ctz(edges[j]);
+        int b = 15 - __builtin_clz((unsigned)edges[j] << 16);
+        adj[a] |= (uint16_t)(1u << b);
+        adj[b] |= (uint16_t)(1u << a);
+    }
+    int cap = 1 << 16;
+    cycle_t *cy = (cycle_t *)malloc(sizeof(cycle_t) * cap);
+    int nc = 0;
+    for (int s = 0; s < 16; s++)
+        cycles_from(adj, s, s, (uint16_t)(1u << s), 1, -1, cy, &nc, cap);
+    free(cy);
+    return nc;
+}

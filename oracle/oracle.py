@@ -1,0 +1,203 @@
+"""ctypes binding for the C oracle (`oracle.c`). Test infrastructure only.
+
+Every function here takes and returns plain Python / numpy values; the enumeration
+functions return (count, nodes, probes, masks) with masks a (count, W) uint64 array sorted
+ascending as multiword integers (word W-1 most significant), or None in counting mode.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+CAP_NONE = -1
+CAP_UBT = -2
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c with gcc (plain -O2, no target-specific flags)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-Wall", "-Wextra",
+                           "-o", tmp, _SRC])
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class _Cond(C.Structure):
+    _fields_ = [("cap", C.c_int32), ("base_facet", C.c_int32),
+                ("forced_in", C.POINTER(C.c_uint64)), ("forced_out", C.POINTER(C.c_uint64)),
+                ("n_affine", C.c_int32), ("c0", C.POINTER(C.c_int32)),
+                ("coef", C.POINTER(C.c_int32))]
+
+
+class _Stats(C.Structure):
+    _fields_ = [("count", C.c_uint64), ("nodes", C.c_uint64), ("probes", C.c_uint64)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            u16p, u32p, u64p = C.POINTER(C.c_uint16), C.POINTER(C.c_uint32), C.POINTER(C.c_uint64)
+            L.orc_candidate_facets.argtypes = [C.c_int, C.c_int, C.c_int, u32p, u16p, C.c_int]
+            L.orc_ridges.argtypes = [C.c_int, C.c_int, u16p, u16p, C.POINTER(C.c_int32), C.c_int]
+            L.orc_kernel_dim.argtypes = [C.c_int, C.c_int, u16p]
+            L.orc_ubt_cap.argtypes = [C.c_int]
+            for name in ("orc_enumerate_brute", "orc_enumerate_dfs"):
+                getattr(L, name).argtypes = [C.c_int, C.c_int, C.c_int, u16p, C.POINTER(_Cond),
+                                             u64p, C.c_uint64, C.POINTER(_Stats)]
+            L.orc_enumerate_sweep.argtypes = [C.c_int, C.c_int, C.c_int, u16p, C.POINTER(_Cond),
+                                              u64p, C.c_uint64, C.POINTER(_Stats), C.c_int]
+            L.orc_n2_cycle_sets.argtypes = [C.c_int, u16p, C.c_int]
+            L.orc_n2_cycle_sets.restype = C.c_long
+            L.orc_n2_cycle_count.argtypes = [C.c_int, u16p]
+            L.orc_n2_cycle_count.restype = C.c_long
+            _lib = L
+    return _lib
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def _check(rc: int, what: str) -> int:
+    if rc < 0:
+        raise OracleError(f"{what} failed with code {rc}")
+    return rc
+
+
+def _p(arr: np.ndarray, ctype):
+    return arr.ctypes.data_as(C.POINTER(ctype))
+
+
+def candidate_facets(kind: str, n: int, m: int, cols: Sequence[int]) -> np.ndarray:
+    """Candidate facets (uint16 vertex masks) in lexicographic order."""
+    k = {"primal": 0, "dual": 1}[kind]
+    c = np.asarray(cols, dtype=np.uint32)
+    out = np.zeros(1 << 16, dtype=np.uint16)
+    M = _check(lib().orc_candidate_facets(k, n, m, _p(c, C.c_uint32), _p(out, C.c_uint16),
+                                          out.size), "candidate_facets")
+    return out[:M].copy()
+
+
+def ridges(n: int, facets: np.ndarray):
+    """(ridge vertex masks in lexicographic order, number of parents of each)."""
+    f = np.ascontiguousarray(facets, dtype=np.uint16)
+    out = np.zeros(1 << 16, dtype=np.uint16)
+    npar = np.zeros(1 << 16, dtype=np.int32)
+    N = _check(lib().orc_ridges(n, f.size, _p(f, C.c_uint16), _p(out, C.c_uint16),
+                                _p(npar, C.c_int32), out.size), "ridges")
+    return out[:N].copy(), npar[:N].copy()
+
+
+def kernel_dim(n: int, facets: np.ndarray) -> int:
+    """dim ker_Z2 A for the ridge-facet incidence matrix of the given facets."""
+    f = np.ascontiguousarray(facets, dtype=np.uint16)
+    return _check(lib().orc_kernel_dim(n, f.size, _p(f, C.c_uint16)), "kernel_dim")
+
+
+def ubt_cap(n: int) -> int:
+    return lib().orc_ubt_cap(n)
+
+
+def _cond(M: int, cap: int, base_facet: bool, forced_in, forced_out, affine):
+    W = (M + 63) // 64
+    keep = []
+    cond = _Cond()
+    cond.cap = cap
+    cond.base_facet = 1 if base_facet else 0
+    for name, val in (("forced_in", forced_in), ("forced_out", forced_out)):
+        if val is None:
+            setattr(cond, name, None)
+        else:
+            a = np.zeros(W, dtype=np.uint64)
+            v = np.asarray(val, dtype=np.uint64).ravel()
+            a[:v.size] = v
+            keep.append(a)
+            setattr(cond, name, _p(a, C.c_uint64))
+    if affine:
+        c0 = np.asarray([g[0] for g in affine], dtype=np.int32)
+        coef = np.ascontiguousarray(np.stack([np.asarray(g[1], dtype=np.int32) for g in affine]))
+        assert coef.shape == (len(affine), M)
+        keep += [c0, coef]
+        cond.n_affine = len(affine)
+        cond.c0 = _p(c0, C.c_int32)
+        cond.coef = _p(coef, C.c_int32)
+    else:
+        cond.n_affine = 0
+    return cond, keep
+
+
+def _enumerate(fn, n, m, facets, cap, base_facet, forced_in, forced_out, affine, list_mode,
+               capacity, extra=()):
+    f = np.ascontiguousarray(facets, dtype=np.uint16)
+    M = f.size
+    W = max(1, (M + 63) // 64)
+    cond, keep = _cond(M, cap, base_facet, forced_in, forced_out, affine)
+    st = _Stats()
+    if list_mode:
+        buf = np.zeros((capacity, W), dtype=np.uint64)
+        rc = fn(n, m, M, _p(f, C.c_uint16), C.byref(cond), _p(buf, C.c_uint64), capacity,
+                C.byref(st), *extra)
+    else:
+        buf = None
+        rc = fn(n, m, M, _p(f, C.c_uint16), C.byref(cond), None, 0, C.byref(st), *extra)
+    if rc == -2 and list_mode:
+        return _enumerate(fn, n, m, facets, cap, base_facet, forced_in, forced_out, affine,
+                          list_mode, int(st.count) + 1, extra)
+    _check(rc, fn.__name__)
+    del keep
+    masks = buf[:st.count].copy() if list_mode else None
+    return int(st.count), int(st.nodes), int(st.probes), masks
+
+
+def enumerate_dfs(n, m, facets, cap=CAP_NONE, base_facet=False, forced_in=None,
+                  forced_out=None, affine=None, list_mode=True, capacity=1 << 12):
+    """O1: ridge-driven canonical search. Returns (count, nodes, probes, masks)."""
+    return _enumerate(lib().orc_enumerate_dfs, n, m, facets, cap, base_facet, forced_in,
+                      forced_out, affine, list_mode, capacity)
+
+
+def enumerate_brute(n, m, facets, cap=CAP_NONE, base_facet=False, forced_in=None,
+                    forced_out=None, affine=None, list_mode=True, capacity=1 << 12):
+    """O3: all 2^M subsets checked by Proposition 2.1."""
+    return _enumerate(lib().orc_enumerate_brute, n, m, facets, cap, base_facet, forced_in,
+                      forced_out, affine, list_mode, capacity)
+
+
+def enumerate_sweep(n, m, facets, cap=CAP_NONE, base_facet=False, forced_in=None,
+                    forced_out=None, affine=None, list_mode=True, capacity=1 << 12, max_s=30):
+    """O2: sweep of ker_Z2 A (Section 2.1)."""
+    return _enumerate(lib().orc_enumerate_sweep, n, m, facets, cap, base_facet, forced_in,
+                      forced_out, affine, list_mode, capacity, extra=(max_s,))
+
+
+def n2_cycle_sets(edges: np.ndarray, max_edges: int = -1) -> int:
+    """O4 (n = 2): families of vertex-disjoint cycles with at most max_edges edges."""
+    e = np.ascontiguousarray(edges, dtype=np.uint16)
+    return _check(lib().orc_n2_cycle_sets(e.size, _p(e, C.c_uint16), max_edges), "n2_cycle_sets")
+
+
+def n2_cycle_count(edges: np.ndarray) -> int:
+    e = np.ascontiguousarray(edges, dtype=np.uint16)
+    return _check(lib().orc_n2_cycle_count(e.size, _p(e, C.c_uint16)), "n2_cycle_count")
+
+
+def instance_facets(inst) -> np.ndarray:
+    return candidate_facets(inst.kind, inst.n, inst.m, inst.cols)
