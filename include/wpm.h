@@ -1,0 +1,187 @@
+/*
+ * wpm.h -- C ABI of the GB300 weak pseudo-manifold enumeration library (libwpm.so).
+ *
+ * The library enumerates every weak pseudo-manifold (WPM) whose facets are drawn from
+ * the candidate facets of a mod-2 characteristic map (Choi, Jang, Vallee, arXiv
+ * 2301.00806). A pure complex K of dimension n-1 on [m] is a WPM when every ridge
+ * ((n-1)-subset) lies in exactly 0 or 2 facets of K: the ridge-facet incidence matrix A
+ * gives A K in {0, 2}^N (Section 2.1, Proposition 2.1). The output for a map lambda and a
+ * set of properties G is
+ *     { K subset of F(lambda) : A K in {0,2}^N and g(K) > 0 for every g in G }
+ * returned as a count and, in list mode, as facet bitmasks.
+ *
+ * Every step after the inputs are copied to the GPU runs in CUDA kernels on the device:
+ * candidate facets, ridges and incidence tables, the search, the output sort.
+ *
+ * Conventions shared by every entry point
+ *   - Vertices are 0..m-1 (m <= 16). A facet is a uint16 vertex mask.
+ *   - Candidate facets are numbered 0..M-1 in lexicographic order of their sorted vertex
+ *     tuples. A facet set (an output K, a forced mask) is a bitmask of
+ *     W = ceil(M/64) uint64 words: facet j is bit j%64 of word j/64.
+ *   - Output masks are sorted ascending as multiword unsigned integers, word W-1 the most
+ *     significant.
+ *   - The empty complex satisfies Proposition 2.1; it is output when every property
+ *     holds at K = 0.
+ *   - Calls are serialised by a library-wide lock; the library allocates and caches its
+ *     device workspace itself (it grows, and is freed by wpm_release_workspace or at
+ *     exit).
+ *   - Every function returns WPM_OK (0) or a negative WPM_ERR_* code; wpm_last_error()
+ *     then describes the failure (thread-local string owned by the library).
+ */
+#ifndef WPM_H
+#define WPM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ----------------------------------------------------------------- */
+#define WPM_OK            0
+#define WPM_ERR_INPUT    -1  /* malformed argument (sizes, rank, repeated dual rows, ...)  */
+#define WPM_ERR_CAPACITY -2  /* an output buffer is too small; wpm_output.count holds the
+                                number of masks needed and nothing was written            */
+#define WPM_ERR_CUDA     -3  /* a CUDA call failed                                        */
+#define WPM_ERR_TIMEOUT  -4  /* a bounded device wait ran out                             */
+#define WPM_ERR_NOMEM    -5  /* device or host allocation failed                          */
+#define WPM_ERR_LIMIT    -6  /* the instance exceeds a library limit below                */
+
+/* ---- limits ------------------------------------------------------------------------ */
+#define WPM_MAX_VERTICES 16    /* m                                                       */
+#define WPM_MAX_FACETS   2048  /* M, candidate facets per instance                        */
+#define WPM_MAX_RIDGES   4096  /* N, ridges with at least one candidate parent            */
+#define WPM_MAX_AFFINE   4     /* general affine properties per instance                  */
+
+/* ---- map forms (Section 3.1) ------------------------------------------------------- */
+#define WPM_LAMBDA_PRIMAL 0  /* lambda_cols[i] = lambda(i) in Z2^n, bit k = row k.
+                                Candidates: n-subsets sigma with lambda(sigma) a basis of
+                                Z2^n (the non-singularity condition).                     */
+#define WPM_LAMBDA_DUAL   1  /* lambda_cols[i] = dual row lambda-bar(i) in Z2^(m-n).
+                                Candidates: n-subsets whose complement indexes a basis of
+                                Z2^(m-n) (linear Gale duality, Proposition 4.2). The rows
+                                must be nonzero, distinct (an injective DCM) and of rank
+                                m-n.                                                     */
+
+/* ---- modes ------------------------------------------------------------------------- */
+#define WPM_MODE_LIST  0  /* count and sorted masks */
+#define WPM_MODE_COUNT 1  /* count only             */
+
+/* ---- the upper-bound-theorem property (Section 4.2) -------------------------------- */
+#define WPM_CAP_NONE -1  /* no bound on |K|                                               */
+#define WPM_CAP_UBT  -2  /* |K| <= f_{n-1}(C^n(n+4)) = C(n+4-ceil(n/2),4)+C(n+3-floor(n/2),4),
+                            the property g(K) = f - |K| + 1 > 0; requires m = n + 4       */
+
+/*
+ * Properties G (Section 2.1 "properties"; Section 4.2; Section 4.4). All pointers are
+ * HOST pointers, read during the call only; NULL / 0 means absent.
+ */
+typedef struct {
+    int32_t ubt_cap;            /* >= 0: |K| <= ubt_cap; WPM_CAP_NONE; WPM_CAP_UBT          */
+    int32_t require_base_facet; /* nonzero: facet {0..n-1} must be in K (the normal form
+                                   lambda = [I_n M] puts facet {1..n} in K, Section 3.1)    */
+    int32_t n_facets;           /* M the masks / coefficient rows below were built for; it
+                                   must equal the instance's M when any of them is given    */
+    const uint64_t *forced_in;  /* ceil(M/64) words: facets that must be in K (Section 4.4,
+                                   condition (1))                                           */
+    const uint64_t *forced_out; /* ceil(M/64) words: facets that must not be in K (Section
+                                   4.4, condition (2))                                      */
+    int32_t n_affine;           /* <= WPM_MAX_AFFINE general properties
+                                   g(K) = c0 + sum_j c_j k_j > 0                             */
+    const int32_t *affine_c0;   /* [n_affine]                                               */
+    const int32_t *affine_coef; /* [n_affine * M], row a = coefficients of property a;
+                                   |c| <= 2^20                                              */
+} wpm_conditions;
+
+/*
+ * Results of one instance. Fields marked "in" are set by the caller, "out" by the library.
+ * In list mode the caller provides `masks` with room for `capacity` masks of
+ * `words_per_mask` words; the pointer is a device pointer when masks_on_device is nonzero.
+ * If the count exceeds `capacity` the call returns WPM_ERR_CAPACITY with `count` set to the
+ * number needed, and the caller re-calls with a larger buffer.
+ */
+typedef struct {
+    uint64_t count;          /* out: number of WPMs (including the empty one if output)   */
+    uint64_t nodes;          /* out: search nodes of the canonical tree                   */
+    uint64_t probes;         /* out: rejected children of the canonical tree              */
+    uint64_t *masks;         /* in: output buffer (list mode), or NULL in count mode      */
+    uint64_t capacity;       /* in: masks the buffer holds                                 */
+    int32_t masks_on_device; /* in: nonzero when `masks` is a device pointer              */
+    int32_t words_per_mask;  /* out: ceil(M/64) (at least 1)                               */
+    int32_t M;               /* out: candidate facets                                      */
+    int32_t N;               /* out: ridges                                                */
+    int32_t status;          /* out: this instance's WPM_* code (batched calls)            */
+    int32_t reserved;
+} wpm_output;
+
+/* One instance of a batch. Pointers are host pointers, read during the call only. */
+typedef struct {
+    int32_t kind;                /* WPM_LAMBDA_PRIMAL or WPM_LAMBDA_DUAL                    */
+    int32_t n;                   /* facet size (dimension + 1), 2..12                       */
+    int32_t m;                   /* vertices, n < m <= 16                                   */
+    int32_t reserved;
+    const uint32_t *lambda_cols; /* m entries, see the map forms above                      */
+    const wpm_conditions *cond;  /* NULL: no properties                                     */
+} wpm_instance;
+
+/*
+ * Search tuning. Zero fields take the library's defaults (a tuned table keyed by the
+ * instance size class). frontier_target: breadth-first frontier items to reach before
+ * depth-first passes; budget: search nodes per thread per depth-first pass;
+ * threads_per_block: 64..512 (multiple of 32); ring_items: capacity of the device work
+ * ring in items.
+ */
+typedef struct {
+    int32_t frontier_target;
+    int32_t budget;
+    int32_t threads_per_block;
+    int32_t reserved;
+    int64_t ring_items;
+} wpm_tuning;
+
+/*
+ * The candidate facets of a map (Section 3.1; Proposition 4.2), in lexicographic order,
+ * computed on the GPU. lambda_cols: host, m entries. facets_out: host buffer of `cap`
+ * entries. Returns M >= 0, or a negative code (WPM_ERR_CAPACITY if cap < M).
+ */
+int wpm_candidate_facets(const uint32_t *lambda_cols, int kind, int n, int m,
+                         uint16_t *facets_out, int cap);
+
+/*
+ * Enumerate the WPMs of one map (Section 2.1 problem statement with the facets of
+ * Proposition 4.2 and the properties of Section 4.2). Blocks until the result is in
+ * `out`. mode: WPM_MODE_LIST or WPM_MODE_COUNT. cond may be NULL.
+ */
+int wpm_enumerate(const uint32_t *lambda_cols, int kind, int n, int m,
+                  const wpm_conditions *cond, wpm_output *out, int mode);
+
+/*
+ * Enumerate the WPMs whose facets come from an arbitrary list (Section 2.1, the most
+ * general input: a set of facets and properties). facets: host, M vertex masks of
+ * popcount n on [m], distinct; they are renumbered in lexicographic order, so masks in
+ * `cond` and in the output refer to that order.
+ */
+int wpm_enumerate_facets(const uint16_t *facets, int M, int n, int m,
+                         const wpm_conditions *cond, wpm_output *out, int mode);
+
+/*
+ * Enumerate `count` instances in one batched run on the GPU: all candidate sets are
+ * built by one launch, the search runs every instance's frontier together, and outputs
+ * are sorted per instance. outs[i] receives instance i (its `status` field holds the
+ * per-instance code; the return value is the first failure, or WPM_OK). tuning may be
+ * NULL. cuda_stream: a cudaStream_t to run on, or NULL for the library's own stream;
+ * the call synchronises that stream before returning.
+ */
+int wpm_enumerate_batch(const wpm_instance *inst, int count, wpm_output *outs, int mode,
+                        const wpm_tuning *tuning, void *cuda_stream);
+
+/* ---- misc -------------------------------------------------------------------------- */
+const char *wpm_last_error(void);
+int wpm_version(void);
+/* Free the cached device workspace of the calling process. */
+void wpm_release_workspace(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WPM_H */

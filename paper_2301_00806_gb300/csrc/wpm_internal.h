@@ -1,0 +1,135 @@
+// wpm_internal.h -- device data layout shared by the kernels (wpm_kernels.cu) and the host
+// runtime (wpm_runtime.cpp) of libwpm. Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace wpm {
+
+constexpr int kMaxVertices = 16;
+constexpr int kMaxFacets = 2048;
+constexpr int kMaxRidges = 4096;
+constexpr int kMaxAffine = 4;
+constexpr int kItemHeader = 4;  // u32 words before In / Out / counters in a work item
+
+// Per-instance error bits written by the device (InstDesc::err).
+enum : uint32_t {
+  kErrLimit = 1u,        // M or N above the library limits
+  kErrMaskSize = 2u,     // condition masks built for another M
+  kErrCapNeedsPic4 = 4u, // WPM_CAP_UBT asked for with m != n + 4
+  kErrNoBase = 8u,       // (not an error: base facet missing means no outputs)
+};
+
+// Work-item flags (word 1, low 16 bits).
+enum : uint32_t {
+  kItemFresh = 1u,  // a root: counters not built, not yet counted as a node
+  kItemOpen = 2u,   // a counted (and, if a WPM, already emitted) node whose remaining
+                    // children are to be explored
+};
+
+// Per-instance counters (ctr[8 * inst + k]).
+enum { kCtrCount = 0, kCtrNodes = 1, kCtrProbes = 2, kCtrFill = 3, kCtrLive = 4, kCtrN = 8 };
+
+// One instance, as the device sees it. The host fills the "in" part and the arena
+// pointers; the setup kernel fills the "derived" part.
+struct InstDesc {
+  // in
+  int32_t kind, n, m, mode;  // kind: 0 primal map, 1 dual map, 2 explicit facet list
+  uint32_t cols[kMaxVertices];
+  int32_t cap_req;      // -1 none, -2 the Section 4.2 bound, >= 0 explicit
+  int32_t base_req;     // require facet {0..n-1}
+  int32_t n_facets_req; // M the condition masks were built for (-1: no masks)
+  int32_t n_aff;
+  int32_t nsub, nrsub;  // C(m, n), C(m, n-1): lex ranks of facets / ridges
+  int32_t has_fin, has_fout;
+  // arena (device pointers), sized by nsub / nrsub
+  uint16_t *facets;     // [nsub] candidate vertex masks, compacted (first M valid)
+  int32_t *fprefix;     // [nsub + 1] exclusive scan of the candidate flag over facet ranks
+  int32_t *rprefix;     // [nrsub + 1] exclusive scan of the has-a-parent flag over ridge ranks
+  int32_t *rtmp;        // [nrsub] scratch (parent count per ridge rank)
+  uint16_t *fr;         // [nsub * n] ridge index of each facet's n ridges
+  int32_t *poff;        // [nrsub + 1] CSR offsets of parents per ridge index
+  uint16_t *pidx;       // [nsub * n] parents, ascending facet index
+  const uint64_t *fin;  // [ceil(M/64)] forced-in mask or null
+  const uint64_t *fout; // [ceil(M/64)] forced-out mask or null
+  const int32_t *aff_c0;   // [n_aff]
+  const int32_t *aff_coef; // [n_aff * M]
+  const uint16_t *given;   // kind 2: the caller's facet list (n_given vertex masks)
+  int32_t n_given, pad0;
+  // derived (setup kernel)
+  int32_t M, N, cap, base_idx;
+  int32_t mw, nw, ow, err;
+  int64_t aff_bound0[kMaxAffine];  // c0 + sum of the positive coefficients
+};
+
+// Output regions of one instance (list mode): `out` and its ping-pong twin `out2` for the
+// merge sort, each `cap` masks of InstDesc::ow words.
+struct OutDesc {
+  uint64_t *out;
+  uint64_t *out2;
+  unsigned long long cap;
+  unsigned long long pad;
+};
+
+// Work ring control (device).
+struct QueueCtl {
+  unsigned long long head;        // next item to take (may overshoot limit)
+  unsigned long long tail;        // next free slot
+  unsigned long long limit;       // items of this pass are [head_start, limit)
+  unsigned long long head_start;
+  unsigned long long err;         // nonzero: ring overflow (items lost)
+  unsigned long long pad[3];
+};
+
+struct PassArgs {
+  const InstDesc *inst;
+  const OutDesc *outs;
+  unsigned long long *ctr;  // [8 * n_inst]
+  uint32_t *ring;           // ring_cap items of item_words u32
+  unsigned long long ring_cap;
+  int item_words;
+  QueueCtl *q;
+  uint32_t *stack;          // [max_depth * n_threads], interleaved by thread
+  int max_depth;
+  int n_threads;            // total threads of the launch (stack stride)
+  long long budget;         // nodes per thread per pass (dfs)
+  unsigned long long dump_limit;  // a thread returns work to the ring only while fewer
+                                  // than this many items are in it (so that every thread
+                                  // dumping max_depth items at once still fits)
+};
+
+// Launchers (wpm_kernels.cu). All return cudaError_t of the launch.
+cudaError_t launch_setup(InstDesc *d_inst, int n_inst, cudaStream_t s);
+cudaError_t launch_roots(const InstDesc *d_inst, int n_ids, const int32_t *d_ids,
+                         unsigned long long *ctr, uint32_t *ring, unsigned long long ring_cap,
+                         int item_words, int cls_mw, QueueCtl *q, cudaStream_t s);
+
+// A kernel size class: compile-time maxima of the u32 words of a facet bitset (mw) and
+// of the packed 2-bit ridge counters (nw).
+struct SizeClass { int mw, nw; };
+int n_size_classes();
+SizeClass size_class(int k);
+int pick_size_class(int mw, int nw);  // smallest class that holds both, or -1
+int item_words_for(int k);            // kItemHeader + 2 * mw + nw of class k
+size_t smem_per_thread(int k);        // dynamic shared bytes per thread of class k
+
+cudaError_t launch_expand(int k, const PassArgs &a, int n_items, int tpb, cudaStream_t s);
+cudaError_t launch_dfs(int k, const PassArgs &a, int blocks, int tpb, cudaStream_t s);
+int dfs_max_blocks_per_sm(int k, int tpb);  // occupancy of the dfs kernel
+
+// One merge pass over the masks of instances d_ids[0..n_ids): instance d_ids[s] holds
+// d_seg[s+1] - d_seg[s] masks; parity 0 merges out -> out2, 1 merges out2 -> out.
+cudaError_t launch_sort_pass(const InstDesc *d_inst, const OutDesc *d_outs, const int32_t *d_ids,
+                             int n_ids, const unsigned long long *d_seg, unsigned long long total,
+                             unsigned long long run, int parity, cudaStream_t s);
+
+// Copy segment s: prefix[s+1] - prefix[s] words from src to dst (device pointers).
+struct CopySeg {
+  const uint64_t *src;
+  uint64_t *dst;
+};
+cudaError_t launch_segment_copy(const CopySeg *d_segs, int n_segs, const unsigned long long *d_prefix,
+                                unsigned long long total_words, cudaStream_t s);
+
+}  // namespace wpm

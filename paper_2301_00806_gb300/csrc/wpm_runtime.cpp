@@ -1,0 +1,729 @@
+// wpm_runtime.cpp -- host runtime and C ABI of libwpm (weak pseudo-manifold enumeration,
+// Choi, Jang, Vallee, arXiv 2301.00806).
+//
+// The host validates arguments, lays out device memory, launches the kernels of
+// wpm_kernels.cu and moves results. It performs none of the enumeration's arithmetic:
+// candidate facets, ridges, incidence, the search and the output sort all run on the GPU.
+//
+// One run (any entry point) is:
+//   upload the instances  ->  setup_kernel (facets, ridges, incidence, properties)
+//   ->  roots_kernel  ->  breadth-first expand passes until the frontier is wide enough
+//   ->  depth-first passes until the work ring is empty  ->  per-instance merge sort
+//   ->  copy-out.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "wpm.h"
+#include "wpm_internal.h"
+
+namespace wpm {
+
+static thread_local std::string t_err;
+
+static int fail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  t_err = buf;
+  return code;
+}
+
+#define CUDA_TRY(x)                                                                   \
+  do {                                                                                \
+    cudaError_t e_ = (x);                                                             \
+    if (e_ != cudaSuccess)                                                            \
+      return fail(WPM_ERR_CUDA, "%s failed: %s", #x, cudaGetErrorString(e_));         \
+  } while (0)
+
+#define WPM_TRY(x)                \
+  do {                            \
+    int r_ = (x);                 \
+    if (r_ != WPM_OK) return r_;  \
+  } while (0)
+
+struct DevBuf {
+  void *p = nullptr;
+  size_t cap = 0;
+  int ensure(size_t bytes) {
+    if (bytes <= cap && p) return WPM_OK;
+    release();
+    size_t want = std::max<size_t>(bytes + bytes / 4, 4096);
+    if (cudaMalloc(&p, want) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+      return fail(WPM_ERR_NOMEM, "cudaMalloc(%zu bytes) failed", want);
+    }
+    cap = want;
+    return WPM_OK;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+  template <class T> T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+struct PinBuf {
+  void *p = nullptr;
+  size_t cap = 0;
+  int ensure(size_t bytes) {
+    if (bytes <= cap && p) return WPM_OK;
+    release();
+    size_t want = std::max<size_t>(bytes + bytes / 4, 4096);
+    if (cudaMallocHost(&p, want) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+      return fail(WPM_ERR_NOMEM, "cudaMallocHost(%zu bytes) failed", want);
+    }
+    cap = want;
+    return WPM_OK;
+  }
+  void release() {
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    cap = 0;
+  }
+  template <class T> T *as() const { return reinterpret_cast<T *>(p); }
+};
+
+// Device buffers reused across calls on one device.
+struct Workspace {
+  int device = -1;
+  int sms = 0;
+  cudaStream_t own = nullptr;
+  DevBuf inst, outd, ctr, arena, cond, ids, q, ring, stack, out, seg, segs, stage;
+  PinBuf h_inst, h_outd, h_q, h_ctr, h_cond, h_ids, h_seg, h_segs, h_stage;
+  void release() {
+    for (DevBuf *b : {&inst, &outd, &ctr, &arena, &cond, &ids, &q, &ring, &stack, &out, &seg,
+                      &segs, &stage})
+      b->release();
+    for (PinBuf *b : {&h_inst, &h_outd, &h_q, &h_ctr, &h_cond, &h_ids, &h_seg, &h_segs, &h_stage})
+      b->release();
+  }
+};
+
+static std::mutex g_mu;
+static std::map<int, Workspace *> g_ws;
+
+static int get_workspace(Workspace **out) {
+  int dev = 0;
+  CUDA_TRY(cudaGetDevice(&dev));
+  auto it = g_ws.find(dev);
+  if (it != g_ws.end()) {
+    *out = it->second;
+    return WPM_OK;
+  }
+  Workspace *w = new Workspace();
+  w->device = dev;
+  CUDA_TRY(cudaDeviceGetAttribute(&w->sms, cudaDevAttrMultiProcessorCount, dev));
+  CUDA_TRY(cudaStreamCreateWithFlags(&w->own, cudaStreamNonBlocking));
+  g_ws[dev] = w;
+  *out = w;
+  return WPM_OK;
+}
+
+static long long binom(int a, int b) {
+  if (b < 0 || b > a) return 0;
+  long long r = 1;
+  for (int i = 0; i < b; i++) r = r * (a - i) / (i + 1);
+  return r;
+}
+
+// An instance as the caller gave it, copied and checked.
+struct HostInst {
+  int kind = 0, n = 0, m = 0;
+  uint32_t cols[kMaxVertices] = {0};
+  std::vector<uint16_t> given;
+  int cap_req = -1, base_req = 0, n_facets_req = -1, n_aff = 0;
+  std::vector<uint64_t> fin, fout;
+  std::vector<int32_t> c0, coef;
+};
+
+static int copy_conditions(const wpm_conditions *c, HostInst &h) {
+  if (!c) return WPM_OK;
+  if (c->ubt_cap < -2) return fail(WPM_ERR_INPUT, "ubt_cap %d is not a cap", c->ubt_cap);
+  h.cap_req = c->ubt_cap;
+  h.base_req = c->require_base_facet ? 1 : 0;
+  if (c->n_affine < 0 || c->n_affine > WPM_MAX_AFFINE)
+    return fail(WPM_ERR_INPUT, "n_affine %d outside 0..%d", c->n_affine, WPM_MAX_AFFINE);
+  const bool masks = c->forced_in || c->forced_out || c->n_affine > 0;
+  if (!masks) return WPM_OK;
+  if (c->n_facets <= 0 || c->n_facets > WPM_MAX_FACETS)
+    return fail(WPM_ERR_INPUT, "n_facets %d: masks and coefficients need the instance's M",
+                c->n_facets);
+  const int M = c->n_facets, W = (M + 63) / 64;
+  h.n_facets_req = M;
+  auto take = [&](const uint64_t *src, std::vector<uint64_t> &dst) {
+    if (!src) return;
+    dst.assign(src, src + W);
+    if (M % 64) dst[W - 1] &= (1ull << (M % 64)) - 1ull;  // bits >= M are not facets
+  };
+  take(c->forced_in, h.fin);
+  take(c->forced_out, h.fout);
+  if (c->n_affine > 0) {
+    if (!c->affine_c0 || !c->affine_coef) return fail(WPM_ERR_INPUT, "affine arrays are NULL");
+    h.n_aff = c->n_affine;
+    h.c0.assign(c->affine_c0, c->affine_c0 + h.n_aff);
+    h.coef.assign(c->affine_coef, c->affine_coef + (size_t)h.n_aff * M);
+    for (int32_t v : h.coef)
+      if (v > (1 << 20) || v < -(1 << 20)) return fail(WPM_ERR_INPUT, "|coefficient| > 2^20");
+  }
+  return WPM_OK;
+}
+
+static int copy_map(const uint32_t *cols, int kind, int n, int m, HostInst &h) {
+  if (kind != WPM_LAMBDA_PRIMAL && kind != WPM_LAMBDA_DUAL)
+    return fail(WPM_ERR_INPUT, "kind %d is neither primal nor dual", kind);
+  if (n < 2 || m <= n || m > WPM_MAX_VERTICES)
+    return fail(WPM_ERR_INPUT, "need 2 <= n < m <= 16 (n=%d, m=%d)", n, m);
+  if (!cols) return fail(WPM_ERR_INPUT, "lambda_cols is NULL");
+  h.kind = kind;
+  h.n = n;
+  h.m = m;
+  const int bits = kind == WPM_LAMBDA_PRIMAL ? n : m - n;
+  for (int i = 0; i < m; i++) {
+    if (bits < 32 && (cols[i] >> bits))
+      return fail(WPM_ERR_INPUT, "column %d has bits above Z2^%d", i, bits);
+    h.cols[i] = cols[i];
+  }
+  if (kind == WPM_LAMBDA_DUAL) {  // an injective DCM: nonzero, pairwise distinct rows
+    for (int i = 0; i < m; i++) {
+      if (cols[i] == 0) return fail(WPM_ERR_INPUT, "dual row %d is zero", i);
+      for (int j = 0; j < i; j++)
+        if (cols[i] == cols[j]) return fail(WPM_ERR_INPUT, "dual rows %d and %d repeat", j, i);
+    }
+  }
+  return WPM_OK;
+}
+
+static int copy_facet_list(const uint16_t *facets, int M, int n, int m, HostInst &h) {
+  if (n < 2 || m <= n || m > WPM_MAX_VERTICES)
+    return fail(WPM_ERR_INPUT, "need 2 <= n < m <= 16 (n=%d, m=%d)", n, m);
+  if (M < 0 || M > WPM_MAX_FACETS) return fail(WPM_ERR_LIMIT, "M=%d outside 0..%d", M, WPM_MAX_FACETS);
+  if (M > 0 && !facets) return fail(WPM_ERR_INPUT, "facets is NULL");
+  h.kind = 2;
+  h.n = n;
+  h.m = m;
+  h.given.assign(facets, facets + M);
+  for (int j = 0; j < M; j++)
+    if (__builtin_popcount(h.given[j]) != n || (h.given[j] >> m))
+      return fail(WPM_ERR_INPUT, "facet %d is not an %d-subset of [%d]", j, n, m);
+  std::vector<uint16_t> s = h.given;
+  std::sort(s.begin(), s.end());
+  if (std::adjacent_find(s.begin(), s.end()) != s.end())
+    return fail(WPM_ERR_INPUT, "repeated facet in the list");
+  return WPM_OK;
+}
+
+// Per-instance outcome of a run.
+struct InstResult {
+  int status = WPM_OK;
+  unsigned long long count = 0, nodes = 0, probes = 0;
+  int M = 0, N = 0, ow = 1;
+};
+
+struct RunOptions {
+  int mode = WPM_MODE_COUNT;
+  int tpb = 0;
+  long long budget = 0;
+  long long frontier_target = 0;
+  long long ring_items = 0;
+  bool setup_only = false;  // stop after the setup kernel (candidate facets)
+};
+
+static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// The engine of every entry point: run the instances `hi` on stream `s`.
+// outs[i] (optional) provides list-mode buffers; res[i] receives the outcome.
+static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, cudaStream_t s,
+               const wpm_output *outs, std::vector<InstResult> &res, std::vector<uint16_t> *facets_out) {
+  const int n_inst = (int)hi.size();
+  res.assign(n_inst, InstResult());
+  if (n_inst == 0) return WPM_OK;
+
+  // ---- device layout of the tables and of the caller's conditions --------------------
+  size_t arena = 0, cond = 0;
+  std::vector<size_t> a_off(n_inst), c_off(n_inst);
+  for (int i = 0; i < n_inst; i++) {
+    const HostInst &h = hi[i];
+    const size_t nsub = binom(h.m, h.n), nrsub = binom(h.m, h.n - 1);
+    a_off[i] = arena;
+    arena += align_up(2 * nsub) + align_up(4 * (nsub + 1)) + align_up(4 * (nrsub + 1)) +
+             align_up(4 * nrsub) + 2 * align_up(2 * nsub * h.n) + align_up(4 * (nrsub + 1));
+    c_off[i] = cond;
+    cond += align_up(8 * h.fin.size()) + align_up(8 * h.fout.size()) + align_up(4 * h.c0.size()) +
+            align_up(4 * h.coef.size()) + align_up(2 * h.given.size());
+  }
+  WPM_TRY(W->arena.ensure(arena));
+  WPM_TRY(W->cond.ensure(cond + 256));
+  WPM_TRY(W->h_cond.ensure(cond + 256));
+  WPM_TRY(W->inst.ensure(sizeof(InstDesc) * n_inst));
+  WPM_TRY(W->h_inst.ensure(sizeof(InstDesc) * n_inst));
+  InstDesc *hd = W->h_inst.as<InstDesc>();
+  char *ab = W->arena.as<char>(), *cb = W->cond.as<char>(), *hc = W->h_cond.as<char>();
+  for (int i = 0; i < n_inst; i++) {
+    const HostInst &h = hi[i];
+    InstDesc &d = hd[i];
+    memset(&d, 0, sizeof(d));
+    d.kind = h.kind;
+    d.n = h.n;
+    d.m = h.m;
+    d.mode = opt.mode;
+    for (int v = 0; v < kMaxVertices; v++) d.cols[v] = h.cols[v];
+    d.cap_req = h.cap_req;
+    d.base_req = h.base_req;
+    d.n_facets_req = h.n_facets_req;
+    d.n_aff = h.n_aff;
+    d.nsub = (int)binom(h.m, h.n);
+    d.nrsub = (int)binom(h.m, h.n - 1);
+    d.has_fin = !h.fin.empty();
+    d.has_fout = !h.fout.empty();
+    size_t o = a_off[i];
+    auto take_a = [&](size_t bytes) { char *p = ab + o; o += align_up(bytes); return p; };
+    d.facets = (uint16_t *)take_a(2 * (size_t)d.nsub);
+    d.fprefix = (int32_t *)take_a(4 * ((size_t)d.nsub + 1));
+    d.rprefix = (int32_t *)take_a(4 * ((size_t)d.nrsub + 1));
+    d.rtmp = (int32_t *)take_a(4 * (size_t)d.nrsub);
+    d.fr = (uint16_t *)take_a(2 * (size_t)d.nsub * h.n);
+    d.poff = (int32_t *)take_a(4 * ((size_t)d.nrsub + 1));
+    d.pidx = (uint16_t *)take_a(2 * (size_t)d.nsub * h.n);
+    size_t c = c_off[i];
+    auto take_c = [&](const void *src, size_t bytes) -> const void * {
+      if (!bytes) return nullptr;
+      memcpy(hc + c, src, bytes);
+      const void *p = cb + c;
+      c += align_up(bytes);
+      return p;
+    };
+    d.fin = (const uint64_t *)take_c(h.fin.data(), 8 * h.fin.size());
+    d.fout = (const uint64_t *)take_c(h.fout.data(), 8 * h.fout.size());
+    d.aff_c0 = (const int32_t *)take_c(h.c0.data(), 4 * h.c0.size());
+    d.aff_coef = (const int32_t *)take_c(h.coef.data(), 4 * h.coef.size());
+    d.given = (const uint16_t *)take_c(h.given.data(), 2 * h.given.size());
+    d.n_given = (int)h.given.size();
+  }
+  if (cond) CUDA_TRY(cudaMemcpyAsync(W->cond.p, W->h_cond.p, cond, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(W->inst.p, hd, sizeof(InstDesc) * n_inst, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(launch_setup(W->inst.as<InstDesc>(), n_inst, s));
+  CUDA_TRY(cudaMemcpyAsync(hd, W->inst.p, sizeof(InstDesc) * n_inst, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+
+  // ---- per-instance checks ----------------------------------------------------------
+  std::vector<int32_t> valid;
+  int mw_max = 1, nw_max = 1, max_depth = 2, max_children = 16;
+  for (int i = 0; i < n_inst; i++) {
+    const InstDesc &d = hd[i];
+    InstResult &r = res[i];
+    r.M = d.M;
+    r.N = d.N;
+    r.ow = d.ow;
+    if (d.err & kErrLimit) {
+      r.status = fail(WPM_ERR_LIMIT, "instance %d: M=%d or N=%d above the limits %d / %d", i, d.M,
+                      d.N, kMaxFacets, kMaxRidges);
+    } else if (d.err & kErrMaskSize) {
+      r.status = fail(WPM_ERR_INPUT, "instance %d: conditions built for M=%d, the map has M=%d", i,
+                      d.n_facets_req, d.M);
+    } else if (d.err & kErrCapNeedsPic4) {
+      r.status = fail(WPM_ERR_INPUT, "instance %d: WPM_CAP_UBT needs m = n + 4", i);
+    } else if (d.kind != 2 && d.M == 0) {
+      r.status = fail(WPM_ERR_INPUT, "instance %d: the map has rank below %d (no candidate facet)",
+                      i, d.kind == 0 ? d.n : d.m - d.n);
+    }
+    if (r.status != WPM_OK) continue;
+    valid.push_back(i);
+    mw_max = std::max(mw_max, d.mw);
+    nw_max = std::max(nw_max, d.nw);
+    const int depth = (d.cap >= 0 ? std::min(d.cap, d.M) : d.M) + 2;
+    max_depth = std::max(max_depth, depth);
+    max_children = std::max(max_children, d.M);
+  }
+  if (facets_out) {
+    if (!valid.empty() && valid[0] == 0) {
+      facets_out->resize(hd[0].M);
+      if (hd[0].M)
+        CUDA_TRY(cudaMemcpy(facets_out->data(), hd[0].facets, 2 * (size_t)hd[0].M,
+                            cudaMemcpyDeviceToHost));
+    }
+    return WPM_OK;
+  }
+  if (opt.setup_only || valid.empty()) return WPM_OK;
+  const int n_valid = (int)valid.size();
+
+  // ---- size class and launch shape ------------------------------------------------
+  const int k = pick_size_class(mw_max, nw_max);
+  if (k < 0) return fail(WPM_ERR_LIMIT, "no kernel size class holds mw=%d nw=%d", mw_max, nw_max);
+  int tpb = opt.tpb > 0 ? opt.tpb : 128;
+  if (tpb != 64 && tpb != 128 && tpb != 256) tpb = 128;
+  int occ = dfs_max_blocks_per_sm(k, tpb);
+  while (occ == 0 && tpb > 64) {
+    tpb /= 2;
+    occ = dfs_max_blocks_per_sm(k, tpb);
+  }
+  if (occ == 0) return fail(WPM_ERR_LIMIT, "size class %d does not fit in shared memory", k);
+  const int blocks = W->sms * occ;
+  const int n_threads = blocks * tpb;
+  const int iw = item_words_for(k);
+  const long long budget = opt.budget > 0 ? opt.budget : 4096;
+  const long long frontier_target = opt.frontier_target > 0 ? opt.frontier_target : 2LL * n_threads;
+  unsigned long long ring_cap =
+      opt.ring_items > 0 ? (unsigned long long)opt.ring_items
+                         : std::max<unsigned long long>(2ull * n_threads * max_depth,
+                                                        std::max(4ull * n_valid, 1ull << 16));
+  ring_cap = std::max<unsigned long long>(ring_cap, (unsigned long long)n_valid + 1);
+  const unsigned long long room = (unsigned long long)n_threads * max_depth;
+  const unsigned long long dump_limit = ring_cap > room ? ring_cap - room : 0;
+
+  // ---- buffers -------------------------------------------------------------------
+  WPM_TRY(W->ctr.ensure(8ull * kCtrN * n_inst));
+  WPM_TRY(W->h_ctr.ensure(8ull * kCtrN * n_inst));
+  WPM_TRY(W->outd.ensure(sizeof(OutDesc) * n_inst));
+  WPM_TRY(W->h_outd.ensure(sizeof(OutDesc) * n_inst));
+  WPM_TRY(W->ids.ensure(4ull * n_inst + 4));
+  WPM_TRY(W->h_ids.ensure(4ull * n_inst + 4));
+  WPM_TRY(W->q.ensure(sizeof(QueueCtl)));
+  WPM_TRY(W->h_q.ensure(sizeof(QueueCtl)));
+  WPM_TRY(W->ring.ensure(ring_cap * iw * 4ull));
+  WPM_TRY(W->stack.ensure((size_t)n_threads * max_depth * 4ull));
+  const bool list = opt.mode == WPM_MODE_LIST;
+  OutDesc *ho = W->h_outd.as<OutDesc>();
+  memset(ho, 0, sizeof(OutDesc) * n_inst);
+  if (list) {
+    size_t total = 0;
+    for (int i : valid) total += align_up(8ull * hd[i].ow * (outs ? outs[i].capacity : 0));
+    WPM_TRY(W->out.ensure(2 * total + 256));
+    char *ob = W->out.as<char>();
+    size_t o = 0;
+    for (int i : valid) {
+      const unsigned long long cap = outs ? outs[i].capacity : 0;
+      const size_t bytes = align_up(8ull * hd[i].ow * cap);
+      ho[i].out = (uint64_t *)(ob + o);
+      ho[i].out2 = (uint64_t *)(ob + total + o);
+      ho[i].cap = cap;
+      o += bytes;
+    }
+  }
+  CUDA_TRY(cudaMemcpyAsync(W->outd.p, ho, sizeof(OutDesc) * n_inst, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemsetAsync(W->ctr.p, 0, 8ull * kCtrN * n_inst, s));
+  int32_t *hids = W->h_ids.as<int32_t>();
+  for (int j = 0; j < n_valid; j++) hids[j] = valid[j];
+  CUDA_TRY(cudaMemcpyAsync(W->ids.p, hids, 4ull * n_valid, cudaMemcpyHostToDevice, s));
+  QueueCtl *hq = W->h_q.as<QueueCtl>();
+  memset(hq, 0, sizeof(QueueCtl));
+  CUDA_TRY(cudaMemcpyAsync(W->q.p, hq, sizeof(QueueCtl), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(launch_roots(W->inst.as<InstDesc>(), n_valid, W->ids.as<int32_t>(),
+                        W->ctr.as<unsigned long long>(), W->ring.as<uint32_t>(), ring_cap, iw,
+                        size_class(k).mw, W->q.as<QueueCtl>(), s));
+  CUDA_TRY(cudaMemcpyAsync(hq, W->q.p, sizeof(QueueCtl), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+
+  PassArgs pa;
+  pa.inst = W->inst.as<InstDesc>();
+  pa.outs = W->outd.as<OutDesc>();
+  pa.ctr = W->ctr.as<unsigned long long>();
+  pa.ring = W->ring.as<uint32_t>();
+  pa.ring_cap = ring_cap;
+  pa.item_words = iw;
+  pa.q = W->q.as<QueueCtl>();
+  pa.stack = W->stack.as<uint32_t>();
+  pa.max_depth = max_depth;
+  pa.n_threads = n_threads;
+  pa.budget = budget;
+  pa.dump_limit = dump_limit;
+
+  // ---- breadth-first expansion, then depth-first passes -----------------------------
+  unsigned long long head = 0, tail = hq->tail;
+  for (;;) {
+    const unsigned long long live = tail - head;
+    if (live == 0 || (long long)live >= frontier_target) break;
+    if (live * (unsigned long long)max_children + live > ring_cap) break;  // children must fit
+    hq->head = tail;
+    hq->tail = tail;
+    hq->limit = tail;
+    hq->head_start = head;
+    hq->err = 0;
+    CUDA_TRY(cudaMemcpyAsync(W->q.p, hq, sizeof(QueueCtl), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(launch_expand(k, pa, (int)live, tpb, s));
+    CUDA_TRY(cudaMemcpyAsync(hq, W->q.p, sizeof(QueueCtl), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (hq->err) return fail(WPM_ERR_NOMEM, "work ring overflow during expansion");
+    head = tail;
+    tail = hq->tail;
+  }
+  while (tail > head) {
+    hq->head = head;
+    hq->tail = tail;
+    hq->limit = tail;
+    hq->head_start = head;
+    hq->err = 0;
+    CUDA_TRY(cudaMemcpyAsync(W->q.p, hq, sizeof(QueueCtl), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(launch_dfs(k, pa, blocks, tpb, s));
+    CUDA_TRY(cudaMemcpyAsync(hq, W->q.p, sizeof(QueueCtl), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (hq->err & 1ull) return fail(WPM_ERR_NOMEM, "work ring overflow (raise ring_items)");
+    if (hq->err & 2ull) return fail(WPM_ERR_LIMIT, "search stack overflow");
+    head = std::min(hq->head, tail);
+    tail = hq->tail;
+  }
+
+  // ---- counters ----------------------------------------------------------------------
+  unsigned long long *hc2 = W->h_ctr.as<unsigned long long>();
+  CUDA_TRY(cudaMemcpyAsync(hc2, W->ctr.p, 8ull * kCtrN * n_inst, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  std::vector<int32_t> sorted_ids;
+  std::vector<unsigned long long> seg(1, 0);
+  unsigned long long max_len = 0;
+  for (int i : valid) {
+    InstResult &r = res[i];
+    const unsigned long long *c = hc2 + kCtrN * i;
+    r.count = c[kCtrCount];
+    r.nodes = c[kCtrNodes];
+    r.probes = c[kCtrProbes];
+    if (list) {
+      const unsigned long long fill = c[kCtrFill];
+      if (fill != r.count)  // every emission reserves one slot
+        return fail(WPM_ERR_CUDA, "instance %d: %llu emitted, %llu slots", i, r.count, fill);
+      if (fill > ho[i].cap) {
+        r.status = fail(WPM_ERR_CAPACITY, "instance %d: %llu masks, capacity %llu", i, fill,
+                        ho[i].cap);
+      } else if (fill > 0) {
+        sorted_ids.push_back(i);
+        seg.push_back(seg.back() + fill);
+        max_len = std::max(max_len, fill);
+      }
+    }
+  }
+  if (!list || sorted_ids.empty()) return WPM_OK;
+
+  // ---- per-instance merge sort on the GPU -----------------------------------------------
+  const int ns = (int)sorted_ids.size();
+  WPM_TRY(W->seg.ensure(8ull * (ns + 1)));
+  WPM_TRY(W->h_seg.ensure(8ull * (ns + 1) + 4ull * ns));
+  WPM_TRY(W->ids.ensure(4ull * n_inst + 4ull * ns + 4));
+  unsigned long long *hseg = W->h_seg.as<unsigned long long>();
+  int32_t *hsid = (int32_t *)(hseg + ns + 1);
+  for (int j = 0; j <= ns; j++) hseg[j] = seg[j];
+  for (int j = 0; j < ns; j++) hsid[j] = sorted_ids[j];
+  int32_t *d_sid = W->ids.as<int32_t>() + n_inst;
+  CUDA_TRY(cudaMemcpyAsync(W->seg.p, hseg, 8ull * (ns + 1), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(d_sid, hsid, 4ull * ns, cudaMemcpyHostToDevice, s));
+  const unsigned long long total = seg.back();
+  int parity = 0;
+  for (unsigned long long runlen = 1; runlen < max_len; runlen *= 2) {
+    CUDA_TRY(launch_sort_pass(W->inst.as<InstDesc>(), W->outd.as<OutDesc>(), d_sid, ns,
+                              W->seg.as<unsigned long long>(), total, runlen, parity, s));
+    parity ^= 1;
+  }
+  if (parity)  // one copying pass brings the result back to `out`
+    CUDA_TRY(launch_sort_pass(W->inst.as<InstDesc>(), W->outd.as<OutDesc>(), d_sid, ns,
+                              W->seg.as<unsigned long long>(), total, 1ull << 62, 1, s));
+
+  // ---- copy-out -------------------------------------------------------------------------
+  std::vector<CopySeg> cs;
+  std::vector<unsigned long long> cp(1, 0);
+  std::vector<int> host_ids;
+  for (int j = 0; j < ns; j++) {
+    const int i = sorted_ids[j];
+    if (outs[i].masks_on_device) continue;
+    host_ids.push_back(i);
+  }
+  size_t stage_words = 0;
+  for (int i : host_ids) stage_words += res[i].count * (unsigned long long)hd[i].ow;
+  WPM_TRY(W->stage.ensure(8 * stage_words + 256));
+  WPM_TRY(W->h_stage.ensure(8 * stage_words + 256));
+  size_t sw = 0;
+  for (int j = 0; j < ns; j++) {
+    const int i = sorted_ids[j];
+    const unsigned long long words = res[i].count * (unsigned long long)hd[i].ow;
+    CopySeg c;
+    c.src = ho[i].out;
+    if (outs[i].masks_on_device) {
+      c.dst = outs[i].masks;
+    } else {
+      c.dst = W->stage.as<uint64_t>() + sw;
+      sw += words;
+    }
+    cs.push_back(c);
+    cp.push_back(cp.back() + words);
+  }
+  WPM_TRY(W->segs.ensure(sizeof(CopySeg) * cs.size() + 8 * cp.size()));
+  WPM_TRY(W->h_segs.ensure(sizeof(CopySeg) * cs.size() + 8 * cp.size()));
+  memcpy(W->h_segs.p, cs.data(), sizeof(CopySeg) * cs.size());
+  memcpy(W->h_segs.as<char>() + sizeof(CopySeg) * cs.size(), cp.data(), 8 * cp.size());
+  CUDA_TRY(cudaMemcpyAsync(W->segs.p, W->h_segs.p, sizeof(CopySeg) * cs.size() + 8 * cp.size(),
+                           cudaMemcpyHostToDevice, s));
+  CUDA_TRY(launch_segment_copy(W->segs.as<CopySeg>(), (int)cs.size(),
+                               (const unsigned long long *)(W->segs.as<char>() +
+                                                            sizeof(CopySeg) * cs.size()),
+                               cp.back(), s));
+  if (sw) CUDA_TRY(cudaMemcpyAsync(W->h_stage.p, W->stage.p, 8 * sw, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  sw = 0;
+  for (int i : host_ids) {
+    const size_t words = res[i].count * (size_t)hd[i].ow;
+    memcpy(outs[i].masks, W->h_stage.as<uint64_t>() + sw, 8 * words);
+    sw += words;
+  }
+  return WPM_OK;
+}
+
+static void fill_output(const InstResult &r, wpm_output *o) {
+  o->count = r.count;
+  o->nodes = r.nodes;
+  o->probes = r.probes;
+  o->words_per_mask = r.ow;
+  o->M = r.M;
+  o->N = r.N;
+  o->status = r.status;
+}
+
+static RunOptions options_from(const wpm_tuning *t, int mode) {
+  RunOptions o;
+  o.mode = mode;
+  if (t) {
+    o.tpb = t->threads_per_block;
+    o.budget = t->budget;
+    o.frontier_target = t->frontier_target;
+    o.ring_items = t->ring_items;
+  }
+  return o;
+}
+
+static int check_output(const wpm_output *out, int mode) {
+  if (!out) return fail(WPM_ERR_INPUT, "out is NULL");
+  if (mode != WPM_MODE_LIST && mode != WPM_MODE_COUNT)
+    return fail(WPM_ERR_INPUT, "mode %d is neither list nor count", mode);
+  if (mode == WPM_MODE_LIST && out->capacity > 0 && !out->masks)
+    return fail(WPM_ERR_INPUT, "list mode with capacity but no buffer");
+  return WPM_OK;
+}
+
+static int single(HostInst &h, wpm_output *out, int mode) {
+  Workspace *W = nullptr;
+  WPM_TRY(get_workspace(&W));
+  std::vector<HostInst> v(1, h);
+  std::vector<InstResult> res;
+  const int rc = run(W, v, options_from(nullptr, mode), W->own, out, res, nullptr);
+  if (rc != WPM_OK) return rc;
+  fill_output(res[0], out);
+  return res[0].status;
+}
+
+}  // namespace wpm
+
+using namespace wpm;
+
+extern "C" {
+
+const char *wpm_last_error(void) { return t_err.c_str(); }
+
+int wpm_version(void) { return 1; }
+
+void wpm_release_workspace(void) {
+  std::lock_guard<std::mutex> g(g_mu);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  auto it = g_ws.find(dev);
+  if (it == g_ws.end()) return;
+  cudaStreamSynchronize(it->second->own);
+  it->second->release();
+  cudaStreamDestroy(it->second->own);
+  delete it->second;
+  g_ws.erase(it);
+}
+
+int wpm_candidate_facets(const uint32_t *lambda_cols, int kind, int n, int m, uint16_t *facets_out,
+                         int cap) {
+  std::lock_guard<std::mutex> g(g_mu);
+  t_err.clear();
+  HostInst h;
+  WPM_TRY(copy_map(lambda_cols, kind, n, m, h));
+  Workspace *W = nullptr;
+  WPM_TRY(get_workspace(&W));
+  std::vector<HostInst> v(1, h);
+  std::vector<InstResult> res;
+  std::vector<uint16_t> f;
+  RunOptions o;
+  o.setup_only = true;
+  WPM_TRY(run(W, v, o, W->own, nullptr, res, &f));
+  if (res[0].status != WPM_OK) return res[0].status;
+  if ((int)f.size() > cap) return fail(WPM_ERR_CAPACITY, "%zu candidate facets, cap %d", f.size(), cap);
+  if (!f.empty()) {
+    if (!facets_out) return fail(WPM_ERR_INPUT, "facets_out is NULL");
+    memcpy(facets_out, f.data(), 2 * f.size());
+  }
+  return (int)f.size();
+}
+
+int wpm_enumerate(const uint32_t *lambda_cols, int kind, int n, int m, const wpm_conditions *cond,
+                  wpm_output *out, int mode) {
+  std::lock_guard<std::mutex> g(g_mu);
+  t_err.clear();
+  WPM_TRY(check_output(out, mode));
+  HostInst h;
+  WPM_TRY(copy_map(lambda_cols, kind, n, m, h));
+  WPM_TRY(copy_conditions(cond, h));
+  return single(h, out, mode);
+}
+
+int wpm_enumerate_facets(const uint16_t *facets, int M, int n, int m, const wpm_conditions *cond,
+                         wpm_output *out, int mode) {
+  std::lock_guard<std::mutex> g(g_mu);
+  t_err.clear();
+  WPM_TRY(check_output(out, mode));
+  HostInst h;
+  WPM_TRY(copy_facet_list(facets, M, n, m, h));
+  WPM_TRY(copy_conditions(cond, h));
+  return single(h, out, mode);
+}
+
+int wpm_enumerate_batch(const wpm_instance *inst, int count, wpm_output *outs, int mode,
+                        const wpm_tuning *tuning, void *cuda_stream) {
+  std::lock_guard<std::mutex> g(g_mu);
+  t_err.clear();
+  if (count < 0 || (count > 0 && (!inst || !outs))) return fail(WPM_ERR_INPUT, "bad batch arrays");
+  std::vector<HostInst> hi;
+  std::vector<int> where;  // hi index -> caller index
+  std::vector<int> status(count, WPM_OK);
+  for (int i = 0; i < count; i++) {
+    int rc = check_output(&outs[i], mode);
+    HostInst h;
+    if (rc == WPM_OK) rc = copy_map(inst[i].lambda_cols, inst[i].kind, inst[i].n, inst[i].m, h);
+    if (rc == WPM_OK) rc = copy_conditions(inst[i].cond, h);
+    status[i] = rc;
+    if (rc == WPM_OK) {
+      hi.push_back(std::move(h));
+      where.push_back(i);
+    }
+  }
+  Workspace *W = nullptr;
+  WPM_TRY(get_workspace(&W));
+  cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : W->own;
+  std::vector<wpm_output> o2(hi.size());
+  for (size_t j = 0; j < hi.size(); j++) o2[j] = outs[where[j]];
+  std::vector<InstResult> res;
+  const int rc = run(W, hi, options_from(tuning, mode), s, o2.data(), res, nullptr);
+  if (rc != WPM_OK) return rc;
+  int first = WPM_OK;
+  for (size_t j = 0; j < hi.size(); j++) {
+    fill_output(res[j], &outs[where[j]]);
+    status[where[j]] = res[j].status;
+  }
+  for (int i = 0; i < count; i++) {
+    outs[i].status = status[i];
+    if (status[i] != WPM_OK && first == WPM_OK) first = status[i];
+  }
+  return first;
+}
+
+}  // extern "C"

@@ -1,0 +1,319 @@
+"""Python binding of libwpm (include/wpm.h): argument marshalling only.
+
+Every function calls the C ABI of the in-tree libwpm.so; all enumeration work runs in its
+CUDA kernels. There is no CPU fallback: without the built library or a CUDA device the
+calls raise.
+
+Masks are returned as numpy uint64 arrays of shape (count, W) with facet j at bit j%64 of
+word j/64, rows sorted ascending as multiword integers (word W-1 most significant), or
+written into a caller's torch CUDA tensor.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+from dataclasses import dataclass
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+OK = 0
+ERR_INPUT = -1
+ERR_CAPACITY = -2
+ERR_CUDA = -3
+ERR_TIMEOUT = -4
+ERR_NOMEM = -5
+ERR_LIMIT = -6
+
+PRIMAL = 0
+DUAL = 1
+MODE_LIST = 0
+MODE_COUNT = 1
+CAP_NONE = -1
+CAP_UBT = -2
+
+_KIND = {"primal": PRIMAL, "dual": DUAL, PRIMAL: PRIMAL, DUAL: DUAL}
+
+
+class WpmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libwpm error {code}: {msg}")
+        self.code = code
+
+
+class Conditions(C.Structure):
+    _fields_ = [("ubt_cap", C.c_int32), ("require_base_facet", C.c_int32),
+                ("n_facets", C.c_int32), ("forced_in", C.POINTER(C.c_uint64)),
+                ("forced_out", C.POINTER(C.c_uint64)), ("n_affine", C.c_int32),
+                ("affine_c0", C.POINTER(C.c_int32)), ("affine_coef", C.POINTER(C.c_int32))]
+
+
+class Output(C.Structure):
+    _fields_ = [("count", C.c_uint64), ("nodes", C.c_uint64), ("probes", C.c_uint64),
+                ("masks", C.POINTER(C.c_uint64)), ("capacity", C.c_uint64),
+                ("masks_on_device", C.c_int32), ("words_per_mask", C.c_int32),
+                ("M", C.c_int32), ("N", C.c_int32), ("status", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class Instance(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("n", C.c_int32), ("m", C.c_int32),
+                ("reserved", C.c_int32), ("lambda_cols", C.POINTER(C.c_uint32)),
+                ("cond", C.POINTER(Conditions))]
+
+
+class Tuning(C.Structure):
+    _fields_ = [("frontier_target", C.c_int32), ("budget", C.c_int32),
+                ("threads_per_block", C.c_int32), ("reserved", C.c_int32),
+                ("ring_items", C.c_int64)]
+
+
+class EngineConfig(C.Structure):
+    _fields_ = [("memory_bytes", C.c_int64), ("max_jobs", C.c_int32), ("budget", C.c_int32),
+                ("max_n", C.c_int32), ("reserved", C.c_int32)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libwpm.so (building it if the sources are newer). Raises if it cannot."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = C.CDLL(path)
+            u16p, u32p, u64p = C.POINTER(C.c_uint16), C.POINTER(C.c_uint32), C.POINTER(C.c_uint64)
+            L.wpm_candidate_facets.argtypes = [u32p, C.c_int, C.c_int, C.c_int, u16p, C.c_int]
+            L.wpm_enumerate.argtypes = [u32p, C.c_int, C.c_int, C.c_int, C.POINTER(Conditions),
+                                        C.POINTER(Output), C.c_int]
+            L.wpm_enumerate_facets.argtypes = [u16p, C.c_int, C.c_int, C.c_int,
+                                               C.POINTER(Conditions), C.POINTER(Output), C.c_int]
+            L.wpm_enumerate_batch.argtypes = [C.POINTER(Instance), C.c_int, C.POINTER(Output),
+                                              C.c_int, C.POINTER(Tuning), C.c_void_p]
+            L.wpm_last_error.restype = C.c_char_p
+            L.wpm_release_workspace.argtypes = []
+            if not hasattr(L, "wpm_engine_create"):
+                _lib = L
+                return _lib
+            L.wpm_engine_create.argtypes = [C.POINTER(EngineConfig), C.c_void_p, C.POINTER(C.c_void_p)]
+            L.wpm_engine_submit.argtypes = [C.c_void_p, C.POINTER(Instance), C.c_int, C.c_uint64,
+                                            C.POINTER(C.c_uint64)]
+            L.wpm_engine_step.argtypes = [C.c_void_p, C.POINTER(C.c_int)]
+            L.wpm_engine_poll.argtypes = [C.c_void_p, u64p, C.c_int]
+            L.wpm_engine_result.argtypes = [C.c_void_p, C.c_uint64, C.POINTER(Output)]
+            L.wpm_engine_destroy.argtypes = [C.c_void_p]
+            L.wpm_engine_destroy.restype = None
+            _lib = L
+    return _lib
+
+
+def _err(code: int) -> WpmError:
+    return WpmError(code, lib().wpm_last_error().decode(errors="replace"))
+
+
+def _p(a: np.ndarray, t):
+    return a.ctypes.data_as(C.POINTER(t))
+
+
+class _Keep:
+    """Holds numpy buffers alive while a ctypes struct points into them."""
+
+    def __init__(self):
+        self.items = []
+
+    def add(self, a):
+        self.items.append(a)
+        return a
+
+
+def _conditions(cap=CAP_NONE, base_facet=False, n_facets=0, forced_in=None, forced_out=None,
+                affine=None, keep: Optional[_Keep] = None) -> Conditions:
+    keep = keep or _Keep()
+    c = Conditions()
+    c.ubt_cap = cap
+    c.require_base_facet = 1 if base_facet else 0
+    c.n_facets = n_facets
+    W = max(1, (n_facets + 63) // 64)
+    for name, val in (("forced_in", forced_in), ("forced_out", forced_out)):
+        if val is None:
+            setattr(c, name, None)
+        else:
+            a = np.zeros(W, dtype=np.uint64)
+            v = np.asarray(val, dtype=np.uint64).ravel()
+            a[:v.size] = v
+            setattr(c, name, _p(keep.add(a), C.c_uint64))
+    if affine:
+        c0 = keep.add(np.asarray([g[0] for g in affine], dtype=np.int32))
+        coef = keep.add(np.ascontiguousarray(np.stack([np.asarray(g[1], dtype=np.int32)
+                                                       for g in affine])))
+        c.n_affine = len(affine)
+        c.affine_c0 = _p(c0, C.c_int32)
+        c.affine_coef = _p(coef, C.c_int32)
+    return c
+
+
+@dataclass
+class Result:
+    count: int
+    nodes: int
+    probes: int
+    M: int
+    N: int
+    words: int
+    masks: Optional[np.ndarray]
+    status: int = OK
+
+
+def _result(o: Output, masks) -> Result:
+    return Result(int(o.count), int(o.nodes), int(o.probes), int(o.M), int(o.N),
+                  int(o.words_per_mask), masks, int(o.status))
+
+
+def candidate_facets(kind, n: int, m: int, cols: Sequence[int]) -> np.ndarray:
+    """Candidate facets (uint16 vertex masks, lexicographic order), computed on the GPU."""
+    cc = np.asarray(cols, dtype=np.uint32)
+    out = np.zeros(1 << 14, dtype=np.uint16)
+    r = lib().wpm_candidate_facets(_p(cc, C.c_uint32), _KIND[kind], n, m, _p(out, C.c_uint16),
+                                   out.size)
+    if r < 0:
+        raise _err(r)
+    return out[:r].copy()
+
+
+def _run_single(call, list_mode: bool, capacity: int) -> Result:
+    while True:
+        o = Output()
+        if list_mode:
+            buf = np.zeros((max(capacity, 1), 16), dtype=np.uint64)  # widest mask: 16 words
+            o.masks = _p(buf, C.c_uint64)
+            o.capacity = capacity
+        r = call(o)
+        if r == ERR_CAPACITY and list_mode:
+            capacity = int(o.count)
+            continue
+        if r != OK:
+            raise _err(r)
+        masks = None
+        if list_mode:
+            w = int(o.words_per_mask)
+            masks = buf.reshape(-1)[: int(o.count) * w].reshape(int(o.count), w).copy()
+        return _result(o, masks)
+
+
+def enumerate(kind, n: int, m: int, cols: Sequence[int], cap=CAP_NONE, base_facet=False,
+              forced_in=None, forced_out=None, affine=None, n_facets=0, list_mode=True,
+              capacity: int = 1 << 14) -> Result:
+    """wpm_enumerate: all WPMs of one map. forced masks / affine rows need n_facets = M."""
+    keep = _Keep()
+    cc = keep.add(np.asarray(cols, dtype=np.uint32))
+    cond = _conditions(cap, base_facet, n_facets, forced_in, forced_out, affine, keep)
+    mode = MODE_LIST if list_mode else MODE_COUNT
+    return _run_single(lambda o: lib().wpm_enumerate(_p(cc, C.c_uint32), _KIND[kind], n, m,
+                                                     C.byref(cond), C.byref(o), mode),
+                       list_mode, capacity)
+
+
+def enumerate_facets(facets: Sequence[int], n: int, m: int, cap=CAP_NONE, base_facet=False,
+                     forced_in=None, forced_out=None, affine=None, list_mode=True,
+                     capacity: int = 1 << 14) -> Result:
+    """wpm_enumerate_facets: WPMs over an explicit facet list (renumbered lexicographically)."""
+    keep = _Keep()
+    f = keep.add(np.asarray(facets, dtype=np.uint16))
+    cond = _conditions(cap, base_facet, f.size if (forced_in is not None or forced_out is not None
+                                                   or affine) else 0,
+                       forced_in, forced_out, affine, keep)
+    mode = MODE_LIST if list_mode else MODE_COUNT
+    return _run_single(lambda o: lib().wpm_enumerate_facets(_p(f, C.c_uint16), f.size, n, m,
+                                                            C.byref(cond), C.byref(o), mode),
+                       list_mode, capacity)
+
+
+@dataclass
+class BatchSpec:
+    kind: object
+    n: int
+    m: int
+    cols: Sequence[int]
+    cap: int = CAP_NONE
+    base_facet: bool = False
+    forced_in: object = None
+    forced_out: object = None
+    affine: object = None
+    n_facets: int = 0
+
+
+def enumerate_batch(specs: List[BatchSpec], list_mode=True, capacities=None, tuning=None,
+                    stream=None, device_out=None) -> List[Result]:
+    """wpm_enumerate_batch over many maps in one batched GPU run.
+
+    capacities: per-instance mask capacity (list mode). device_out: optional list of torch
+    CUDA uint64 tensors (one per instance, capacity x W) to receive the masks on the device;
+    then Result.masks is None and the tensors hold the sorted masks. stream: a torch CUDA
+    stream (or raw cudaStream_t int)."""
+    n = len(specs)
+    keep = _Keep()
+    insts = (Instance * max(n, 1))()
+    outs = (Output * max(n, 1))()
+    conds = []
+    bufs = []
+    for i in range(n):
+        s = specs[i]
+        cc = keep.add(np.asarray(s.cols, dtype=np.uint32))
+        cond = _conditions(s.cap, s.base_facet, s.n_facets, s.forced_in, s.forced_out, s.affine,
+                           keep)
+        conds.append(cond)
+        insts[i].kind = _KIND[s.kind]
+        insts[i].n = s.n
+        insts[i].m = s.m
+        insts[i].lambda_cols = _p(cc, C.c_uint32)
+        insts[i].cond = C.pointer(cond)
+        if list_mode:
+            cap = int(capacities[i]) if capacities is not None else (1 << 12)
+            if device_out is not None:
+                t = device_out[i]
+                outs[i].masks = C.cast(C.c_void_p(t.data_ptr()), C.POINTER(C.c_uint64))
+                outs[i].masks_on_device = 1
+                outs[i].capacity = cap
+                bufs.append(None)
+            else:
+                buf = np.zeros(max(cap, 1) * 16, dtype=np.uint64)
+                bufs.append(buf)
+                outs[i].masks = _p(buf, C.c_uint64)
+                outs[i].capacity = cap
+        else:
+            bufs.append(None)
+    tun = None
+    if tuning:
+        tun = Tuning()
+        for k, v in tuning.items():
+            setattr(tun, k, v)
+    st = None
+    if stream is not None:
+        st = stream if isinstance(stream, int) else stream.cuda_stream
+    r = lib().wpm_enumerate_batch(insts, n, outs, MODE_LIST if list_mode else MODE_COUNT,
+                                  C.byref(tun) if tun is not None else None,
+                                  C.c_void_p(st) if st else None)
+    if r not in (OK, ERR_CAPACITY):
+        raise _err(r)
+    res = []
+    for i in range(n):
+        o = outs[i]
+        masks = None
+        if list_mode and bufs[i] is not None and o.status == OK:
+            w = int(o.words_per_mask)
+            masks = bufs[i][: int(o.count) * w].reshape(int(o.count), w).copy()
+        res.append(_result(o, masks))
+    return res
+
+
+def release_workspace() -> None:
+    lib().wpm_release_workspace()

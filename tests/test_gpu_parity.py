@@ -1,0 +1,320 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle, element by element.
+
+Everything is integer work, so the bar is bit-exact: the same sorted list of facet masks,
+the same count, and the same node and probe counts of the canonical search tree.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from conftest import load_table
+from paper_2301_00806_gb300 import instances as I
+
+pytestmark = pytest.mark.gpu
+
+T2 = load_table("table2_line7.txt")
+
+
+@pytest.fixture(scope="module")
+def W():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2301_00806_gb300 import wpm
+    wpm.lib()
+    return wpm
+
+
+def oracle_run(inst, **kw):
+    f = O.instance_facets(inst)
+    return f, O.enumerate_dfs(inst.n, inst.m, f, capacity=1 << 15, **kw)
+
+
+def assert_same(gpu, orc, nodes=True):
+    c, nd, pr, masks = orc
+    assert gpu.count == c
+    if nodes:
+        assert (gpu.nodes, gpu.probes) == (nd, pr)
+    if masks is not None and gpu.masks is not None:
+        assert gpu.masks.shape == masks.shape
+        assert np.array_equal(gpu.masks, masks)
+
+
+# ---------------------------------------------------------------------------------------
+# candidate facets
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", range(2, 12))
+def test_candidate_facets_match(W, n):
+    for rows in I.idcm_orbit_reps(n)[:5]:
+        assert np.array_equal(W.candidate_facets("dual", n, n + 4, rows),
+                              O.candidate_facets("dual", n, n + 4, rows))
+    inst = I.single_dual(n, 3) if n <= 11 else None
+    assert np.array_equal(W.candidate_facets("dual", n, n + 4, inst.cols), O.instance_facets(inst))
+
+
+def test_candidate_facets_primal(W):
+    for s in range(16):
+        inst = I.fano_primal(s)
+        assert np.array_equal(W.candidate_facets("primal", 3, 7, inst.cols), O.instance_facets(inst))
+
+
+# ---------------------------------------------------------------------------------------
+# single instances: the Fano map (n=3, m=7) and the n=5 dual maps
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", range(16))
+@pytest.mark.parametrize("cap", [-1, -2])
+def test_fano_all_seeds(W, seed, cap):
+    inst = I.fano_primal(seed)
+    f, orc = oracle_run(inst, cap=cap)
+    g = W.enumerate("primal", 3, 7, inst.cols, cap=cap)
+    assert g.M == 28 and g.N == 21
+    assert g.count == (666 if cap == -2 else 1303)
+    assert_same(g, orc)
+
+
+@pytest.mark.parametrize("seed", range(16))
+def test_n5_dual_seeds(W, seed):
+    inst = I.single_dual(5, seed)
+    f, orc = oracle_run(inst, cap=-2)
+    g = W.enumerate("dual", 5, 9, inst.cols, cap=-2)
+    assert_same(g, orc)
+
+
+def test_count_mode_equals_list_mode(W):
+    inst = I.single_dual(6, 1)
+    a = W.enumerate("dual", 6, 10, inst.cols, cap=-2, list_mode=True, capacity=1 << 16)
+    b = W.enumerate("dual", 6, 10, inst.cols, cap=-2, list_mode=False)
+    assert (a.count, a.nodes, a.probes) == (b.count, b.nodes, b.probes)
+    assert b.masks is None
+
+
+@pytest.mark.parametrize("n", [6, 7])
+def test_larger_single_instances(W, n):
+    inst = I.single_dual(n, 0)
+    f, orc = oracle_run(inst, cap=-2)
+    g = W.enumerate("dual", n, n + 4, inst.cols, cap=-2, capacity=1 << 17)
+    assert_same(g, orc)
+
+
+# ---------------------------------------------------------------------------------------
+# Table 2, first row, through the batched entry point
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("row", [r for r in T2 if r[0] <= 7], ids=[f"n{r[0]}" for r in T2 if r[0] <= 7])
+def test_table2_batched_against_oracle_and_paper(W, row):
+    n, want = row
+    reps = I.idcm_orbit_reps(n)
+    specs = [W.BatchSpec("dual", n, n + 4, r, cap=-2, base_facet=True) for r in reps]
+    res = W.enumerate_batch(specs, list_mode=False)
+    assert sum(r.count for r in res) == want
+    if n <= 5:
+        for r, rows in zip(res, reps):
+            f = O.candidate_facets("dual", n, n + 4, rows)
+            c, nd, pr, _ = O.enumerate_dfs(n, n + 4, f, cap=-2, base_facet=True, list_mode=False)
+            assert (r.count, r.nodes, r.probes) == (c, nd, pr)
+
+
+def test_table2_n4_lists(W):
+    reps = I.idcm_orbit_reps(4)
+    specs = [W.BatchSpec("dual", 4, 8, r, cap=-2, base_facet=True) for r in reps]
+    res = W.enumerate_batch(specs, list_mode=True, capacities=[4096] * len(reps))
+    for r, rows in zip(res, reps):
+        f = O.candidate_facets("dual", 4, 8, rows)
+        assert_same(r, O.enumerate_dfs(4, 8, f, cap=-2, base_facet=True, capacity=4096))
+
+
+# ---------------------------------------------------------------------------------------
+# mixed batch, and the work-splitting paths forced by extreme tuning
+# ---------------------------------------------------------------------------------------
+
+def _mixed(count=48, seed=11):
+    return [inst for inst in I.batch_duals(count, 3, 6, seed=seed)]
+
+
+@pytest.mark.parametrize("tuning", [None,
+                                    {"budget": 1},
+                                    {"budget": 7, "frontier_target": 1},
+                                    {"budget": 64, "frontier_target": 100000},
+                                    {"budget": 3, "ring_items": 3000, "threads_per_block": 64},
+                                    {"budget": 1000000, "frontier_target": 1, "threads_per_block": 256}],
+                         ids=["default", "budget1", "nofrontier", "wide", "smallring", "nobudget"])
+def test_mixed_batch_with_tunings(W, tuning):
+    insts = _mixed()
+    orc = [oracle_run(inst, cap=-2)[1] for inst in insts]
+    specs = [W.BatchSpec("dual", i.n, i.m, i.cols, cap=-2) for i in insts]
+    res = W.enumerate_batch(specs, list_mode=True, capacities=[o[0] + 1 for o in orc], tuning=tuning)
+    for g, o in zip(res, orc):
+        assert g.status == 0
+        assert_same(g, o)
+
+
+def test_batch_into_device_tensors(W):
+    import torch
+    insts = _mixed(12, seed=3)
+    orc = [oracle_run(inst, cap=-2)[1] for inst in insts]
+    caps = [o[0] for o in orc]
+    # int64 storage viewed as uint64 words; room for 4 words per mask (M <= 256)
+    outs = [torch.zeros((max(c, 1), 4), dtype=torch.int64, device="cuda") for c in caps]
+    specs = [W.BatchSpec("dual", i.n, i.m, i.cols, cap=-2) for i in insts]
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream()
+    res = W.enumerate_batch(specs, list_mode=True, capacities=caps, device_out=outs, stream=stream)
+    for g, o, t in zip(res, orc, outs):
+        assert g.count == o[0]
+        flat = t.flatten()[: g.count * g.words].cpu().numpy().view(np.uint64)
+        assert np.array_equal(flat.reshape(-1, g.words), o[3])
+
+
+# ---------------------------------------------------------------------------------------
+# properties: forced facets, affine functions, explicit facet lists
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", range(24))
+def test_random_properties(W, seed):
+    rng = np.random.default_rng(500 + seed)
+    n = int(rng.integers(3, 6))
+    inst = I.single_dual(n, seed)
+    f = O.instance_facets(inst)
+    M = f.size
+    kw = {"cap": int(rng.choice([-1, -2, int(rng.integers(3, 40))]))}
+    words = (M + 63) // 64
+    if seed % 3 == 0:
+        fi = np.zeros(words, dtype=np.uint64)
+        j = int(rng.integers(0, M))
+        fi[j // 64] |= np.uint64(1) << np.uint64(j % 64)
+        kw["forced_in"] = fi
+    if seed % 4 == 0:
+        fo = np.zeros(words, dtype=np.uint64)
+        for j in rng.choice(M, size=min(M, 6), replace=False):
+            fo[j // 64] |= np.uint64(1) << np.uint64(int(j) % 64)
+        kw["forced_out"] = fo
+    if seed % 2 == 1:
+        kw["affine"] = [(int(rng.integers(0, 30)), rng.integers(-2, 3, size=M).tolist())
+                        for _ in range(int(rng.integers(1, 4)))]
+    if seed % 5 == 2:
+        kw["base_facet"] = True
+    orc = O.enumerate_dfs(n, n + 4, f, capacity=1 << 15, **kw)
+    g = W.enumerate("dual", n, n + 4, inst.cols, n_facets=M, capacity=1 << 15, **kw)
+    assert_same(g, orc)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_explicit_facet_lists(W, seed):
+    rng = np.random.default_rng(900 + seed)
+    n = int(rng.integers(2, 5))
+    m = int(rng.integers(n + 2, min(16, n + 6) + 1))
+    import itertools
+    allf = [sum(1 << v for v in c) for c in itertools.combinations(range(m), n)]
+    k = int(min(len(allf), rng.integers(8, 60)))
+    pick = sorted(rng.choice(len(allf), size=k, replace=False).tolist())
+    facets = np.array([allf[i] for i in pick], dtype=np.uint16)
+    shuffled = facets.copy()
+    rng.shuffle(shuffled)
+    cap = int(rng.choice([-1, 12]))
+    orc = O.enumerate_dfs(n, m, facets, cap=cap, capacity=1 << 16)
+    g = W.enumerate_facets(shuffled, n, m, cap=cap, capacity=1 << 16)
+    assert g.M == k
+    assert_same(g, orc)
+
+
+# ---------------------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------------------
+
+def test_empty_facet_list(W):
+    g = W.enumerate_facets([], 3, 7)
+    assert g.count == 1 and g.M == 0 and g.masks.shape == (1, 1) and int(g.masks[0, 0]) == 0
+
+
+@pytest.mark.parametrize("n", range(2, 13))
+def test_simplex_boundary(W, n):
+    inst = I.simplex_boundary_primal(n)
+    g = W.enumerate("primal", n, n + 1, inst.cols)
+    assert g.M == n + 1 and g.count == 2
+    assert [int(x) for x in g.masks[:, 0]] == [0, (1 << (n + 1)) - 1]
+    assert_same(g, O.enumerate_dfs(n, n + 1, O.instance_facets(inst)))
+
+
+def test_cap_zero_and_base_facet_missing(W):
+    inst = I.single_dual(4, 0)
+    g = W.enumerate("dual", 4, 8, inst.cols, cap=0)
+    assert g.count == 1 and int(g.masks[0, 0]) == 0
+    f = O.instance_facets(inst)
+    orc = O.enumerate_dfs(4, 8, f, base_facet=True, cap=-2)
+    g = W.enumerate("dual", 4, 8, inst.cols, base_facet=True, cap=-2)
+    assert_same(g, orc)
+
+
+def test_capacity_error_reports_the_count(W):
+    inst = I.fano_primal(2)
+    from paper_2301_00806_gb300.wpm import Output, _p, lib
+    import ctypes as C
+    cols = np.asarray(inst.cols, dtype=np.uint32)
+    buf = np.zeros(10, dtype=np.uint64)
+    o = Output()
+    o.masks = _p(buf, C.c_uint64)
+    o.capacity = 10
+    r = lib().wpm_enumerate(_p(cols, C.c_uint32), 0, 3, 7, None, C.byref(o), 0)
+    assert r == W.ERR_CAPACITY and o.count == 1303 and not buf.any()
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(kind="dual", n=5, m=9, cols=[1, 2, 3, 3, 4, 5, 6, 7, 8]), -1),   # repeated rows
+    (dict(kind="dual", n=3, m=7, cols=[1, 2, 3, 4, 5, 6, 7]), -1),          # rank 3 < 4
+    (dict(kind="dual", n=5, m=9, cols=[0, 2, 3, 4, 5, 6, 7, 8, 9]), -1),    # zero row
+    (dict(kind="primal", n=1, m=3, cols=[1, 1, 1]), -1),                     # n < 2
+    (dict(kind="primal", n=3, m=17, cols=list(range(1, 18))), -1),          # m > 16
+    (dict(kind="primal", n=2, m=4, cols=[1, 2, 4, 3]), -1),                  # bit above Z2^2
+])
+def test_invalid_inputs(W, kw, code):
+    with pytest.raises(W.WpmError) as e:
+        W.enumerate(kw["kind"], kw["n"], kw["m"], kw["cols"])
+    assert e.value.code == code
+
+
+def test_ubt_needs_picard4(W):
+    with pytest.raises(W.WpmError):
+        W.enumerate("primal", 3, 8, [1, 2, 4, 3, 5, 6, 7, 1], cap=-2)
+
+
+def test_limit_exceeded(W):
+    import itertools
+    rng = np.random.default_rng(7)
+    # a generic primal map of rank 8 on 16 vertices: thousands of 8-subsets are bases
+    cols = [1 << i for i in range(8)] + rng.integers(1, 256, size=8).tolist()
+    with pytest.raises(W.WpmError) as e:
+        W.enumerate("primal", 8, 16, cols)
+    assert e.value.code == W.ERR_LIMIT
+    # 2000 facets of size 8 on 16 vertices have far more than 4096 ridges
+    allf = [sum(1 << v for v in c) for c in itertools.combinations(range(16), 8)]
+    pick = rng.choice(len(allf), size=2000, replace=False)
+    with pytest.raises(W.WpmError) as e:
+        W.enumerate_facets([allf[i] for i in pick], 8, 16)
+    assert e.value.code == W.ERR_LIMIT
+
+
+# ---------------------------------------------------------------------------------------
+# every output is a WPM (Proposition 2.1), checked from vertex masks at a larger size
+# ---------------------------------------------------------------------------------------
+
+def test_outputs_are_wpms_n8(W):
+    from collections import Counter
+    inst = I.single_dual(8, 5)
+    f = W.candidate_facets("dual", 8, 12, inst.cols)
+    g = W.enumerate("dual", 8, 12, inst.cols, cap=-2, capacity=1 << 18)
+    rng = np.random.default_rng(0)
+    for row in g.masks[rng.choice(g.count, size=min(300, g.count), replace=False)]:
+        fac = [int(f[j]) for j in range(f.size) if (int(row[j // 64]) >> (j % 64)) & 1]
+        deg = Counter()
+        for x in fac:
+            v = x
+            while v:
+                low = v & -v
+                deg[x ^ low] += 1
+                v ^= low
+        assert all(d == 2 for d in deg.values())
+        assert len(fac) <= I.ubt_cap(8)
+    keys = [tuple(int(w) for w in reversed(r)) for r in g.masks]
+    assert keys == sorted(keys) and len(set(keys)) == len(keys)
