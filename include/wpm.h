@@ -127,7 +127,7 @@ typedef struct {
 /*
  * Search tuning. Zero fields take the library's defaults (a tuned table keyed by the
  * instance size class). frontier_target: breadth-first frontier items to reach before
- * depth-first passes; budget: search nodes per thread per depth-first pass;
+ * depth-first passes; budget: most search nodes per thread per depth-first pass;
  * threads_per_block: 64..512 (multiple of 32); ring_items: capacity of the device work
  * ring in items.
  */
@@ -135,7 +135,8 @@ typedef struct {
     int32_t frontier_target;
     int32_t budget;
     int32_t threads_per_block;
-    int32_t reserved;
+    int32_t idle_percent;   /* a depth-first pass ends (busy threads return their work to
+                               the ring) once this percentage of threads is idle; 0 = 50 */
     int64_t ring_items;
 } wpm_tuning;
 

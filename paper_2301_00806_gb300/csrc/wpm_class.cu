@@ -10,17 +10,13 @@
 namespace wpm {
 
 #define X(id, mw, nw)                                                                       \
-  cudaError_t class_launch_##id(bool expand, const PassArgs &a, int grid, int n_items,     \
-                                int tpb, cudaStream_t s) {                                 \
-    if (tpb == 64) return launch_t<mw, nw, 64>(expand, a, grid, n_items, s);               \
-    if (tpb == 128) return launch_t<mw, nw, 128>(expand, a, grid, n_items, s);             \
-    return launch_t<mw, nw, 256>(expand, a, grid, n_items, s);                             \
+  cudaError_t class_launch_##id(int mode, const PassArgs &a, int grid, int n_items, int tpb, \
+                                size_t smem, cudaStream_t s) {                             \
+    return launch_t<mw, nw>(mode, a, grid, n_items, tpb, smem, s);                         \
   }                                                                                         \
-  int class_occupancy_##id(int tpb) {                                                       \
-    if (tpb == 64) return occupancy_t<mw, nw, 64>();                                        \
-    if (tpb == 128) return occupancy_t<mw, nw, 128>();                                      \
-    return occupancy_t<mw, nw, 256>();                                                      \
-  }
+  int class_occupancy_##id(int tpb, size_t smem) { return occupancy_t<mw, nw>(tpb, smem); } \
+  static_assert(Cls<mw, nw>::SMW == ((nw + 2 * mw + 1) & ~1) + 4 * kMaxAffine,            \
+                "state_words() in wpm_kernels.cu must match Cls::SMW");
 WPM_ONE_CLASS(X, WPM_CLASS_ID)
 #undef X
 

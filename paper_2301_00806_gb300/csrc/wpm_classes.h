@@ -33,9 +33,9 @@
 namespace wpm {
 struct PassArgs;
 #define X(id, mw, nw)                                                                       \
-  cudaError_t class_launch_##id(bool expand, const PassArgs &a, int grid, int n_items,     \
-                                int tpb, cudaStream_t s);                                  \
-  int class_occupancy_##id(int tpb);
+  cudaError_t class_launch_##id(int mode, const PassArgs &a, int grid, int n_items, int tpb, \
+                                size_t smem, cudaStream_t s);                              \
+  int class_occupancy_##id(int tpb, size_t smem);
 WPM_CLASSES(X)
 #undef X
 }  // namespace wpm

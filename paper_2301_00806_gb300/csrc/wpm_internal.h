@@ -21,11 +21,16 @@ enum : uint32_t {
   kErrNoBase = 8u,       // (not an error: base facet missing means no outputs)
 };
 
-// Work-item flags (word 1, low 16 bits).
+// Work items: u32 words [inst, flags | floor << 16, size | base << 16, acc], then In[MW],
+// Out[MW], cnt[NW]. Flags (word 1, low 16 bits):
 enum : uint32_t {
-  kItemFresh = 1u,  // a root: counters not built, not yet counted as a node
-  kItemOpen = 2u,   // a counted (and, if a WPM, already emitted) node whose remaining
-                    // children are to be explored
+  kItemFresh = 1u,      // a root: counters not built, not yet counted as a node
+  kItemOpen = 2u,       // a counted (and, if a WPM, already emitted) node whose children
+                        // have not been counted: the receiver expands it
+  kItemSeed = 4u,       // a WPM node part-way through its new-lowest-facet children: they
+                        // continue from the window at `base` (facets below are done)
+  kItemSeedValid = 8u,  // ... whose window is already checked: `acc` holds its accepted
+                        // positions not yet explored
 };
 
 // Per-instance counters (ctr[8 * inst + k]).
@@ -47,10 +52,11 @@ struct InstDesc {
   uint16_t *facets;     // [nsub] candidate vertex masks, compacted (first M valid)
   int32_t *fprefix;     // [nsub + 1] exclusive scan of the candidate flag over facet ranks
   int32_t *rprefix;     // [nrsub + 1] exclusive scan of the has-a-parent flag over ridge ranks
-  int32_t *rtmp;        // [nrsub] scratch (parent count per ridge rank)
-  uint16_t *fr;         // [nsub * n] ridge index of each facet's n ridges
-  int32_t *poff;        // [nrsub + 1] CSR offsets of parents per ridge index
-  uint16_t *pidx;       // [nsub * n] parents, ascending facet index
+  uint16_t *frw;        // [nsub * fstride] row j: the n ridge indices of facet j
+  uint16_t *prw;        // [nrsub * pstride] row r: the parents of ridge r, ascending facet
+                        // index, padded with 0xFFFF (at most m - n + 1 <= 15 parents)
+  int32_t fstride;      // 8 when n <= 8, else 16
+  int32_t pstride;      // 8 when m - n + 1 <= 8, else 16
   const uint64_t *fin;  // [ceil(M/64)] forced-in mask or null
   const uint64_t *fout; // [ceil(M/64)] forced-out mask or null
   const int32_t *aff_c0;   // [n_aff]
@@ -79,7 +85,9 @@ struct QueueCtl {
   unsigned long long limit;       // items of this pass are [head_start, limit)
   unsigned long long head_start;
   unsigned long long err;         // nonzero: ring overflow (items lost)
-  unsigned long long pad[3];
+  unsigned long long idle;        // warps of this pass that have stopped
+  unsigned long long nodes;       // nodes searched in this pass (tracing)
+  unsigned long long pad;
 };
 
 struct PassArgs {
@@ -90,12 +98,13 @@ struct PassArgs {
   unsigned long long ring_cap;
   int item_words;
   QueueCtl *q;
-  uint32_t *stack;          // [max_depth * n_threads], interleaved by thread
-  int max_depth;
-  int n_threads;            // total threads of the launch (stack stride)
-  long long budget;         // nodes per thread per pass (dfs)
-  unsigned long long dump_limit;  // a thread returns work to the ring only while fewer
-                                  // than this many items are in it (so that every thread
+  int max_depth;            // stack entries per warp (shared memory)
+  int pad0;
+  long long budget;         // nodes per warp per pass (dfs)
+  unsigned long long idle_limit;  // once this many warps of a pass have stopped, the
+                                  // others return their remaining work and stop too
+  unsigned long long dump_limit;  // a warp returns work to the ring only while fewer
+                                  // than this many items are in it (so that every warp
                                   // dumping max_depth items at once still fits)
 };
 
@@ -112,11 +121,13 @@ int n_size_classes();
 SizeClass size_class(int k);
 int pick_size_class(int mw, int nw);  // smallest class that holds both, or -1
 int item_words_for(int k);            // kItemHeader + 2 * mw + nw of class k
-size_t smem_per_thread(int k);        // dynamic shared bytes per thread of class k
+int state_words(int k);               // shared u32 words of one warp's search state
 
+// One warp per item / per search; tpb is a multiple of 32 (at most 256).
 cudaError_t launch_expand(int k, const PassArgs &a, int n_items, int tpb, cudaStream_t s);
 cudaError_t launch_dfs(int k, const PassArgs &a, int blocks, int tpb, cudaStream_t s);
-int dfs_max_blocks_per_sm(int k, int tpb);  // occupancy of the dfs kernel
+size_t dfs_smem_bytes(int k, int tpb, int max_depth);
+int dfs_max_blocks_per_sm(int k, int tpb, int max_depth);  // occupancy of the dfs kernel
 
 // One merge pass over the masks of instances d_ids[0..n_ids): instance d_ids[s] holds
 // d_seg[s+1] - d_seg[s] masks; parity 0 merges out -> out2, 1 merges out2 -> out.

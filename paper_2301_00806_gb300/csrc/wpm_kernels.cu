@@ -130,6 +130,8 @@ __global__ void __launch_bounds__(256) setup_kernel(InstDesc *insts) {
   uint32_t cols[kMaxVertices];
   for (int v = 0; v < kMaxVertices; v++) cols[v] = I.cols[v];
   const uint32_t all = (1u << m) - 1u;
+  const int fstride = n <= 8 ? 8 : 16;           // u16 entries per facet row
+  const int pstride = m - n + 1 <= 8 ? 8 : 16;   // u16 entries per ridge row
 
   // (a1) candidate facets: lambda(sigma) a basis (primal) or the complement's dual rows a
   // basis (dual, Proposition 4.2).
@@ -149,42 +151,41 @@ __global__ void __launch_bounds__(256) setup_kernel(InstDesc *insts) {
   // (a2) ridges: (n-1)-subsets with at least one candidate parent, lexicographic order.
   for (int R = t; R < nrsub; R += T) {
     uint32_t r = unrank(R, m, n - 1, C);
-    int cnt = 0;
-    for (int v = 0; v < m; v++) {
+    int has = 0;
+    for (int v = 0; v < m && !has; v++) {
       if ((r >> v) & 1u) continue;
       int F = rank_of(r | (1u << v), m, n, C);
-      cnt += I.fprefix[F + 1] - I.fprefix[F];
+      has = I.fprefix[F + 1] - I.fprefix[F];
     }
-    I.rtmp[R] = cnt;
-    I.rprefix[R] = cnt > 0;
+    I.rprefix[R] = has;
   }
   __syncthreads();
   const int N = block_scan(I.rprefix, nrsub, tmp);
-  for (int R = t; R < nrsub; R += T)
-    if (I.rprefix[R + 1] != I.rprefix[R]) I.poff[I.rprefix[R]] = I.rtmp[R];
-  __syncthreads();
-  block_scan(I.poff, N, tmp);
-  // parents of each ridge in ascending facet index: adding a larger vertex to the same
-  // ridge gives a lexicographically larger facet
+  // the parents row of each ridge, ascending facet index: adding a larger vertex to the
+  // same ridge gives a lexicographically larger facet
   for (int R = t; R < nrsub; R += T) {
     if (I.rprefix[R + 1] == I.rprefix[R]) continue;
     uint32_t r = unrank(R, m, n - 1, C);
-    int k = I.poff[I.rprefix[R]];
+    uint16_t *row = I.prw + pstride * (size_t)I.rprefix[R];
+    int k = 0;
     for (int v = 0; v < m; v++) {
       if ((r >> v) & 1u) continue;
       int F = rank_of(r | (1u << v), m, n, C);
-      if (I.fprefix[F + 1] != I.fprefix[F]) I.pidx[k++] = (uint16_t)I.fprefix[F];
+      if (I.fprefix[F + 1] != I.fprefix[F]) row[k++] = (uint16_t)I.fprefix[F];
     }
+    for (; k < pstride; k++) row[k] = 0xFFFFu;
   }
-  // the n ridges of each facet
+  // the ridges row of each facet
   for (int j = t; j < M; j += T) {
     uint32_t f = I.facets[j];
+    uint16_t *row = I.frw + fstride * (size_t)j;
     int k = 0;
     for (int v = 0; v < m; v++) {
       if (!((f >> v) & 1u)) continue;
       int R = rank_of(f & ~(1u << v), m, n - 1, C);
-      I.fr[j * n + k++] = (uint16_t)I.rprefix[R];
+      row[k++] = (uint16_t)I.rprefix[R];
     }
+    for (; k < fstride; k++) row[k] = 0;
   }
 
   // (a3) properties: sum of the positive coefficients of each affine property
@@ -217,6 +218,8 @@ __global__ void __launch_bounds__(256) setup_kernel(InstDesc *insts) {
     I.mw = (M + 31) / 32;
     I.nw = (N + 15) / 16;
     I.ow = M > 0 ? (M + 63) / 64 : 1;
+    I.fstride = fstride;
+    I.pstride = pstride;
     I.err = err;
   }
 }
@@ -291,18 +294,20 @@ int pick_size_class(int mw, int nw) {
   return -1;
 }
 int item_words_for(int k) { return kItemHeader + 2 * kClasses[k].mw + kClasses[k].nw; }
-size_t smem_per_thread(int k) {
-  const int mw = kClasses[k].mw, nw = kClasses[k].nw;
-  const int sw = nw <= 64 ? 0 : (nw + 31) / 32;
-  return (size_t)(nw + 2 * mw + sw) * 4u;
+int state_words(int k) {  // must equal Cls<mw, nw>::SMW of wpm_search.cuh
+  return ((kClasses[k].nw + 2 * kClasses[k].mw + 1) & ~1) + 4 * kMaxAffine;
 }
 
-static cudaError_t dispatch(int k, bool expand, const PassArgs &a, int grid, int n_items, int tpb,
-                            cudaStream_t s) {
+size_t dfs_smem_bytes(int k, int tpb, int max_depth) {
+  return (size_t)(tpb / 32) * (size_t)(state_words(k) + 2 * max_depth) * 4u;
+}
+
+static cudaError_t dispatch(int k, int mode, const PassArgs &a, int grid, int n_items, int tpb,
+                            size_t smem, cudaStream_t s) {
   switch (k) {
 #define X(id, mw, nw) \
   case id:            \
-    return class_launch_##id(expand, a, grid, n_items, tpb, s);
+    return class_launch_##id(mode, a, grid, n_items, tpb, smem, s);
     WPM_CLASSES(X)
 #undef X
     default:
@@ -310,11 +315,12 @@ static cudaError_t dispatch(int k, bool expand, const PassArgs &a, int grid, int
   }
 }
 
-int dfs_max_blocks_per_sm(int k, int tpb) {
+int dfs_max_blocks_per_sm(int k, int tpb, int max_depth) {
+  const size_t smem = dfs_smem_bytes(k, tpb, max_depth);
   switch (k) {
 #define X(id, mw, nw) \
   case id:            \
-    return class_occupancy_##id(tpb);
+    return class_occupancy_##id(tpb, smem);
     WPM_CLASSES(X)
 #undef X
     default:
@@ -324,11 +330,13 @@ int dfs_max_blocks_per_sm(int k, int tpb) {
 
 cudaError_t launch_expand(int k, const PassArgs &a, int n_items, int tpb, cudaStream_t s) {
   if (n_items <= 0) return cudaSuccess;
-  return dispatch(k, true, a, (n_items + tpb - 1) / tpb, n_items, tpb, s);
+  const int wpb = tpb / 32;
+  const size_t smem = (size_t)wpb * state_words(k) * 4u;
+  return dispatch(k, 0, a, (n_items + wpb - 1) / wpb, n_items, tpb, smem, s);
 }
 
 cudaError_t launch_dfs(int k, const PassArgs &a, int blocks, int tpb, cudaStream_t s) {
-  return dispatch(k, false, a, blocks, 0, tpb, s);
+  return dispatch(k, 1, a, blocks, 0, tpb, dfs_smem_bytes(k, tpb, a.max_depth), s);
 }
 
 // ------------------------------------------------------------------------------------

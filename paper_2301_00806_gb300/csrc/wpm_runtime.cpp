@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -102,11 +103,11 @@ struct Workspace {
   int device = -1;
   int sms = 0;
   cudaStream_t own = nullptr;
-  DevBuf inst, outd, ctr, arena, cond, ids, q, ring, stack, out, seg, segs, stage;
+  DevBuf inst, outd, ctr, arena, cond, ids, q, ring, out, seg, segs, stage;
   PinBuf h_inst, h_outd, h_q, h_ctr, h_cond, h_ids, h_seg, h_segs, h_stage;
   void release() {
-    for (DevBuf *b : {&inst, &outd, &ctr, &arena, &cond, &ids, &q, &ring, &stack, &out, &seg,
-                      &segs, &stage})
+    for (DevBuf *b : {&inst, &outd, &ctr, &arena, &cond, &ids, &q, &ring, &out, &seg, &segs,
+                      &stage})
       b->release();
     for (PinBuf *b : {&h_inst, &h_outd, &h_q, &h_ctr, &h_cond, &h_ids, &h_seg, &h_segs, &h_stage})
       b->release();
@@ -239,6 +240,7 @@ struct RunOptions {
   long long budget = 0;
   long long frontier_target = 0;
   long long ring_items = 0;
+  int idle_percent = 0;
   bool setup_only = false;  // stop after the setup kernel (candidate facets)
 };
 
@@ -260,7 +262,7 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
     const size_t nsub = binom(h.m, h.n), nrsub = binom(h.m, h.n - 1);
     a_off[i] = arena;
     arena += align_up(2 * nsub) + align_up(4 * (nsub + 1)) + align_up(4 * (nrsub + 1)) +
-             align_up(4 * nrsub) + 2 * align_up(2 * nsub * h.n) + align_up(4 * (nrsub + 1));
+             align_up(32 * nsub) + align_up(32 * nrsub);
     c_off[i] = cond;
     cond += align_up(8 * h.fin.size()) + align_up(8 * h.fout.size()) + align_up(4 * h.c0.size()) +
             align_up(4 * h.coef.size()) + align_up(2 * h.given.size());
@@ -294,10 +296,8 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
     d.facets = (uint16_t *)take_a(2 * (size_t)d.nsub);
     d.fprefix = (int32_t *)take_a(4 * ((size_t)d.nsub + 1));
     d.rprefix = (int32_t *)take_a(4 * ((size_t)d.nrsub + 1));
-    d.rtmp = (int32_t *)take_a(4 * (size_t)d.nrsub);
-    d.fr = (uint16_t *)take_a(2 * (size_t)d.nsub * h.n);
-    d.poff = (int32_t *)take_a(4 * ((size_t)d.nrsub + 1));
-    d.pidx = (uint16_t *)take_a(2 * (size_t)d.nsub * h.n);
+    d.frw = (uint16_t *)take_a(32 * (size_t)d.nsub);
+    d.prw = (uint16_t *)take_a(32 * (size_t)d.nrsub);
     size_t c = c_off[i];
     auto take_c = [&](const void *src, size_t bytes) -> const void * {
       if (!bytes) return nullptr;
@@ -363,25 +363,27 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
   // ---- size class and launch shape ------------------------------------------------
   const int k = pick_size_class(mw_max, nw_max);
   if (k < 0) return fail(WPM_ERR_LIMIT, "no kernel size class holds mw=%d nw=%d", mw_max, nw_max);
-  int tpb = opt.tpb > 0 ? opt.tpb : 128;
-  if (tpb != 64 && tpb != 128 && tpb != 256) tpb = 128;
-  int occ = dfs_max_blocks_per_sm(k, tpb);
+  int tpb = opt.tpb > 0 ? opt.tpb : 256;
+  if (tpb != 64 && tpb != 128 && tpb != 256) tpb = 256;
+  int occ = dfs_max_blocks_per_sm(k, tpb, max_depth);
   while (occ == 0 && tpb > 64) {
     tpb /= 2;
-    occ = dfs_max_blocks_per_sm(k, tpb);
+    occ = dfs_max_blocks_per_sm(k, tpb, max_depth);
   }
-  if (occ == 0) return fail(WPM_ERR_LIMIT, "size class %d does not fit in shared memory", k);
+  if (occ == 0)
+    return fail(WPM_ERR_LIMIT, "size class %d with depth %d does not fit in shared memory", k,
+                max_depth);
   const int blocks = W->sms * occ;
-  const int n_threads = blocks * tpb;
+  const int n_warps = blocks * (tpb / 32);
   const int iw = item_words_for(k);
-  const long long budget = opt.budget > 0 ? opt.budget : 4096;
-  const long long frontier_target = opt.frontier_target > 0 ? opt.frontier_target : 2LL * n_threads;
+  const long long budget = opt.budget > 0 ? opt.budget : (1ll << 40);
+  const long long frontier_target = opt.frontier_target > 0 ? opt.frontier_target : 2LL * n_warps;
   unsigned long long ring_cap =
       opt.ring_items > 0 ? (unsigned long long)opt.ring_items
-                         : std::max<unsigned long long>(2ull * n_threads * max_depth,
+                         : std::max<unsigned long long>(2ull * n_warps * max_depth,
                                                         std::max(4ull * n_valid, 1ull << 16));
   ring_cap = std::max<unsigned long long>(ring_cap, (unsigned long long)n_valid + 1);
-  const unsigned long long room = (unsigned long long)n_threads * max_depth;
+  const unsigned long long room = (unsigned long long)n_warps * max_depth;
   const unsigned long long dump_limit = ring_cap > room ? ring_cap - room : 0;
 
   // ---- buffers -------------------------------------------------------------------
@@ -394,7 +396,6 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
   WPM_TRY(W->q.ensure(sizeof(QueueCtl)));
   WPM_TRY(W->h_q.ensure(sizeof(QueueCtl)));
   WPM_TRY(W->ring.ensure(ring_cap * iw * 4ull));
-  WPM_TRY(W->stack.ensure((size_t)n_threads * max_depth * 4ull));
   const bool list = opt.mode == WPM_MODE_LIST;
   OutDesc *ho = W->h_outd.as<OutDesc>();
   memset(ho, 0, sizeof(OutDesc) * n_inst);
@@ -435,11 +436,22 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
   pa.ring_cap = ring_cap;
   pa.item_words = iw;
   pa.q = W->q.as<QueueCtl>();
-  pa.stack = W->stack.as<uint32_t>();
   pa.max_depth = max_depth;
-  pa.n_threads = n_threads;
   pa.budget = budget;
   pa.dump_limit = dump_limit;
+  const int idle_pct = (opt.idle_percent > 0 && opt.idle_percent <= 100) ? opt.idle_percent : 50;
+  pa.idle_limit = std::max<unsigned long long>(1, (unsigned long long)n_warps * idle_pct / 100);
+  const bool trace = getenv("WPM_TRACE") != nullptr;
+  if (trace)
+    fprintf(stderr, "[wpm] %d instances, class %d (mw %d nw %d), %d blocks x %d threads, budget %lld, "
+            "ring %llu items of %d words, max depth %d\n", n_valid, k, size_class(k).mw,
+            size_class(k).nw, blocks, tpb, budget, ring_cap, iw, max_depth);
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  if (trace) {
+    cudaEventCreate(&ev0);
+    cudaEventCreate(&ev1);
+  }
+  int pass_no = 0;
 
   // ---- breadth-first expansion, then depth-first passes -----------------------------
   unsigned long long head = 0, tail = hq->tail;
@@ -452,11 +464,21 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
     hq->limit = tail;
     hq->head_start = head;
     hq->err = 0;
+    hq->idle = 0;
+    hq->nodes = 0;
     CUDA_TRY(cudaMemcpyAsync(W->q.p, hq, sizeof(QueueCtl), cudaMemcpyHostToDevice, s));
+    if (trace) cudaEventRecord(ev0, s);
     CUDA_TRY(launch_expand(k, pa, (int)live, tpb, s));
+    if (trace) cudaEventRecord(ev1, s);
     CUDA_TRY(cudaMemcpyAsync(hq, W->q.p, sizeof(QueueCtl), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     if (hq->err) return fail(WPM_ERR_NOMEM, "work ring overflow during expansion");
+    if (trace) {
+      float ms = 0;
+      cudaEventElapsedTime(&ms, ev0, ev1);
+      fprintf(stderr, "[wpm] expand %d: %llu items -> %llu items, %.3f ms\n", pass_no++, live,
+              hq->tail - tail, ms);
+    }
     head = tail;
     tail = hq->tail;
   }
@@ -466,12 +488,23 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
     hq->limit = tail;
     hq->head_start = head;
     hq->err = 0;
+    hq->idle = 0;
+    hq->nodes = 0;
     CUDA_TRY(cudaMemcpyAsync(W->q.p, hq, sizeof(QueueCtl), cudaMemcpyHostToDevice, s));
+    if (trace) cudaEventRecord(ev0, s);
     CUDA_TRY(launch_dfs(k, pa, blocks, tpb, s));
+    if (trace) cudaEventRecord(ev1, s);
     CUDA_TRY(cudaMemcpyAsync(hq, W->q.p, sizeof(QueueCtl), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     if (hq->err & 1ull) return fail(WPM_ERR_NOMEM, "work ring overflow (raise ring_items)");
     if (hq->err & 2ull) return fail(WPM_ERR_LIMIT, "search stack overflow");
+    if (trace) {
+      float ms = 0;
+      cudaEventElapsedTime(&ms, ev0, ev1);
+      fprintf(stderr, "[wpm] dfs %d: %llu items, %llu taken, %llu new, %llu nodes, %.3f ms\n",
+              pass_no++, tail - head, std::min(hq->head, tail) - head, hq->tail - tail, hq->nodes,
+              ms);
+    }
     head = std::min(hq->head, tail);
     tail = hq->tail;
   }
@@ -595,6 +628,7 @@ static RunOptions options_from(const wpm_tuning *t, int mode) {
     o.budget = t->budget;
     o.frontier_target = t->frontier_target;
     o.ring_items = t->ring_items;
+    o.idle_percent = t->idle_percent;
   }
   return o;
 }

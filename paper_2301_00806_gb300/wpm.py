@@ -67,7 +67,7 @@ class Instance(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("frontier_target", C.c_int32), ("budget", C.c_int32),
-                ("threads_per_block", C.c_int32), ("reserved", C.c_int32),
+                ("threads_per_block", C.c_int32), ("idle_percent", C.c_int32),
                 ("ring_items", C.c_int64)]
 
 
