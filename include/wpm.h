@@ -135,9 +135,12 @@ typedef struct {
     int32_t frontier_target;
     int32_t budget;
     int32_t threads_per_block;
-    int32_t idle_percent;   /* a depth-first pass ends (busy threads return their work to
-                               the ring) once this percentage of threads is idle; 0 = 50 */
+    int32_t idle_percent;   /* a depth-first pass ends (busy searches return their work to
+                               the ring) once this percentage of searches is idle; 0 = 50 */
     int64_t ring_items;
+    int32_t search;         /* 1: one search per thread, 2: one search per warp, 0: by size
+                               (per thread up to n = 9)                                    */
+    int32_t reserved;
 } wpm_tuning;
 
 /*

@@ -32,10 +32,11 @@
 
 namespace wpm {
 struct PassArgs;
+// mode 0: warp expansion, 1: warp depth-first pass, 2: thread depth-first pass
 #define X(id, mw, nw)                                                                       \
   cudaError_t class_launch_##id(int mode, const PassArgs &a, int grid, int n_items, int tpb, \
                                 size_t smem, cudaStream_t s);                              \
-  int class_occupancy_##id(int tpb, size_t smem);
+  int class_occupancy_##id(int mode, int tpb, size_t smem);
 WPM_CLASSES(X)
 #undef X
 }  // namespace wpm

@@ -85,9 +85,12 @@ struct QueueCtl {
   unsigned long long limit;       // items of this pass are [head_start, limit)
   unsigned long long head_start;
   unsigned long long err;         // nonzero: ring overflow (items lost)
-  unsigned long long idle;        // warps of this pass that have stopped
+  unsigned long long idle;        // searches of this pass that have stopped
   unsigned long long nodes;       // nodes searched in this pass (tracing)
   unsigned long long pad;
+  // tracing of per-thread passes (PassArgs::trace): warp loop iterations, and the lanes
+  // that in them took a search step, fetched an item, returned work, or had stopped
+  unsigned long long iters, lanes_step, lanes_fetch, lanes_dump, lanes_stopped, pad2[3];
 };
 
 struct PassArgs {
@@ -98,13 +101,17 @@ struct PassArgs {
   unsigned long long ring_cap;
   int item_words;
   QueueCtl *q;
-  int max_depth;            // stack entries per warp (shared memory)
-  int pad0;
-  long long budget;         // nodes per warp per pass (dfs)
-  unsigned long long idle_limit;  // once this many warps of a pass have stopped, the
+  int max_depth;            // stack entries per search
+  int n_threads;            // threads of a per-thread launch (stride of `stack`)
+  uint32_t *stack;          // per-thread search: [max_depth * n_threads]
+  long long *aff_scratch;   // per-thread search: [n_threads * 2 * kMaxAffine]
+  long long budget;         // nodes per search per pass (dfs)
+  int trace;                // nonzero: count loop iterations and lane activity
+  int pad1;
+  unsigned long long idle_limit;  // once this many searches of a pass have stopped, the
                                   // others return their remaining work and stop too
-  unsigned long long dump_limit;  // a warp returns work to the ring only while fewer
-                                  // than this many items are in it (so that every warp
+  unsigned long long dump_limit;  // a search returns work to the ring only while fewer
+                                  // than this many items are in it (so that every search
                                   // dumping max_depth items at once still fits)
 };
 
@@ -121,13 +128,18 @@ int n_size_classes();
 SizeClass size_class(int k);
 int pick_size_class(int mw, int nw);  // smallest class that holds both, or -1
 int item_words_for(int k);            // kItemHeader + 2 * mw + nw of class k
-int state_words(int k);               // shared u32 words of one warp's search state
+int state_words(int k);               // shared u32 words of one warp search's state
+int tstate_words(int k);              // shared u32 words of one thread search's state
 
-// One warp per item / per search; tpb is a multiple of 32 (at most 256).
+// Search modes of the depth-first passes.
+enum { kSearchThread = 1, kSearchWarp = 2 };
+
+// Breadth-first expansion: one warp per item; tpb a multiple of 32 (at most 256).
 cudaError_t launch_expand(int k, const PassArgs &a, int n_items, int tpb, cudaStream_t s);
-cudaError_t launch_dfs(int k, const PassArgs &a, int blocks, int tpb, cudaStream_t s);
-size_t dfs_smem_bytes(int k, int tpb, int max_depth);
-int dfs_max_blocks_per_sm(int k, int tpb, int max_depth);  // occupancy of the dfs kernel
+// Depth-first pass in the given search mode (tpb 64, 128 or 256).
+cudaError_t launch_dfs(int k, int search, const PassArgs &a, int blocks, int tpb, cudaStream_t s);
+size_t dfs_smem_bytes(int k, int search, int tpb, int max_depth);
+int dfs_max_blocks_per_sm(int k, int search, int tpb, int max_depth);
 
 // One merge pass over the masks of instances d_ids[0..n_ids): instance d_ids[s] holds
 // d_seg[s+1] - d_seg[s] masks; parity 0 merges out -> out2, 1 merges out2 -> out.

@@ -298,7 +298,13 @@ int state_words(int k) {  // must equal Cls<mw, nw>::SMW of wpm_search.cuh
   return ((kClasses[k].nw + 2 * kClasses[k].mw + 1) & ~1) + 4 * kMaxAffine;
 }
 
-size_t dfs_smem_bytes(int k, int tpb, int max_depth) {
+int tstate_words(int k) {  // must equal ts::TCls<mw, nw, *>::SMW of wpm_tsearch.cuh
+  const int nw = kClasses[k].nw, mw = kClasses[k].mw;
+  return nw + 2 * mw + (nw <= 64 ? 0 : (nw + 31) / 32);
+}
+
+size_t dfs_smem_bytes(int k, int search, int tpb, int max_depth) {
+  if (search == kSearchThread) return (size_t)tpb * tstate_words(k) * 4u;
   return (size_t)(tpb / 32) * (size_t)(state_words(k) + 2 * max_depth) * 4u;
 }
 
@@ -315,12 +321,13 @@ static cudaError_t dispatch(int k, int mode, const PassArgs &a, int grid, int n_
   }
 }
 
-int dfs_max_blocks_per_sm(int k, int tpb, int max_depth) {
-  const size_t smem = dfs_smem_bytes(k, tpb, max_depth);
+int dfs_max_blocks_per_sm(int k, int search, int tpb, int max_depth) {
+  const size_t smem = dfs_smem_bytes(k, search, tpb, max_depth);
+  const int mode = search == kSearchThread ? 2 : 1;
   switch (k) {
 #define X(id, mw, nw) \
   case id:            \
-    return class_occupancy_##id(tpb, smem);
+    return class_occupancy_##id(mode, tpb, smem);
     WPM_CLASSES(X)
 #undef X
     default:
@@ -335,8 +342,9 @@ cudaError_t launch_expand(int k, const PassArgs &a, int n_items, int tpb, cudaSt
   return dispatch(k, 0, a, (n_items + wpb - 1) / wpb, n_items, tpb, smem, s);
 }
 
-cudaError_t launch_dfs(int k, const PassArgs &a, int blocks, int tpb, cudaStream_t s) {
-  return dispatch(k, 1, a, blocks, 0, tpb, dfs_smem_bytes(k, tpb, a.max_depth), s);
+cudaError_t launch_dfs(int k, int search, const PassArgs &a, int blocks, int tpb, cudaStream_t s) {
+  return dispatch(k, search == kSearchThread ? 2 : 1, a, blocks, 0, tpb,
+                  dfs_smem_bytes(k, search, tpb, a.max_depth), s);
 }
 
 // ------------------------------------------------------------------------------------

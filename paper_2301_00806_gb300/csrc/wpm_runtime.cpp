@@ -103,11 +103,11 @@ struct Workspace {
   int device = -1;
   int sms = 0;
   cudaStream_t own = nullptr;
-  DevBuf inst, outd, ctr, arena, cond, ids, q, ring, out, seg, segs, stage;
+  DevBuf inst, outd, ctr, arena, cond, ids, q, ring, stack, aff, out, seg, segs, stage;
   PinBuf h_inst, h_outd, h_q, h_ctr, h_cond, h_ids, h_seg, h_segs, h_stage;
   void release() {
-    for (DevBuf *b : {&inst, &outd, &ctr, &arena, &cond, &ids, &q, &ring, &out, &seg, &segs,
-                      &stage})
+    for (DevBuf *b : {&inst, &outd, &ctr, &arena, &cond, &ids, &q, &ring, &stack, &aff, &out, &seg,
+                      &segs, &stage})
       b->release();
     for (PinBuf *b : {&h_inst, &h_outd, &h_q, &h_ctr, &h_cond, &h_ids, &h_seg, &h_segs, &h_stage})
       b->release();
@@ -241,6 +241,7 @@ struct RunOptions {
   long long frontier_target = 0;
   long long ring_items = 0;
   int idle_percent = 0;
+  int search = 0;
   bool setup_only = false;  // stop after the setup kernel (candidate facets)
 };
 
@@ -363,27 +364,34 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
   // ---- size class and launch shape ------------------------------------------------
   const int k = pick_size_class(mw_max, nw_max);
   if (k < 0) return fail(WPM_ERR_LIMIT, "no kernel size class holds mw=%d nw=%d", mw_max, nw_max);
-  int tpb = opt.tpb > 0 ? opt.tpb : 256;
-  if (tpb != 64 && tpb != 128 && tpb != 256) tpb = 256;
-  int occ = dfs_max_blocks_per_sm(k, tpb, max_depth);
+  // per-thread searches for small instances; per-warp searches where a thread's state would
+  // leave too few searches per SM
+  const int search = opt.search == kSearchThread || opt.search == kSearchWarp
+                         ? opt.search
+                         : (k <= 5 ? kSearchThread : kSearchWarp);
+  int tpb = opt.tpb > 0 ? opt.tpb : (search == kSearchThread ? 128 : 256);
+  if (tpb != 64 && tpb != 128 && tpb != 256) tpb = 128;
+  int occ = dfs_max_blocks_per_sm(k, search, tpb, max_depth);
   while (occ == 0 && tpb > 64) {
     tpb /= 2;
-    occ = dfs_max_blocks_per_sm(k, tpb, max_depth);
+    occ = dfs_max_blocks_per_sm(k, search, tpb, max_depth);
   }
   if (occ == 0)
     return fail(WPM_ERR_LIMIT, "size class %d with depth %d does not fit in shared memory", k,
                 max_depth);
   const int blocks = W->sms * occ;
-  const int n_warps = blocks * (tpb / 32);
+  const int n_threads = blocks * tpb;
+  const int n_searches = search == kSearchThread ? n_threads : n_threads / 32;
   const int iw = item_words_for(k);
   const long long budget = opt.budget > 0 ? opt.budget : (1ll << 40);
-  const long long frontier_target = opt.frontier_target > 0 ? opt.frontier_target : 2LL * n_warps;
+  const long long frontier_target =
+      opt.frontier_target > 0 ? opt.frontier_target : 2LL * n_searches;
   unsigned long long ring_cap =
       opt.ring_items > 0 ? (unsigned long long)opt.ring_items
-                         : std::max<unsigned long long>(2ull * n_warps * max_depth,
+                         : std::max<unsigned long long>(2ull * n_searches * max_depth,
                                                         std::max(4ull * n_valid, 1ull << 16));
   ring_cap = std::max<unsigned long long>(ring_cap, (unsigned long long)n_valid + 1);
-  const unsigned long long room = (unsigned long long)n_warps * max_depth;
+  const unsigned long long room = (unsigned long long)n_searches * max_depth;
   const unsigned long long dump_limit = ring_cap > room ? ring_cap - room : 0;
 
   // ---- buffers -------------------------------------------------------------------
@@ -396,6 +404,10 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
   WPM_TRY(W->q.ensure(sizeof(QueueCtl)));
   WPM_TRY(W->h_q.ensure(sizeof(QueueCtl)));
   WPM_TRY(W->ring.ensure(ring_cap * iw * 4ull));
+  if (search == kSearchThread) {
+    WPM_TRY(W->stack.ensure((size_t)n_threads * max_depth * 4ull));
+    WPM_TRY(W->aff.ensure((size_t)n_threads * 2 * kMaxAffine * 8ull));
+  }
   const bool list = opt.mode == WPM_MODE_LIST;
   OutDesc *ho = W->h_outd.as<OutDesc>();
   memset(ho, 0, sizeof(OutDesc) * n_inst);
@@ -437,15 +449,20 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
   pa.item_words = iw;
   pa.q = W->q.as<QueueCtl>();
   pa.max_depth = max_depth;
+  pa.n_threads = n_threads;
+  pa.stack = search == kSearchThread ? W->stack.as<uint32_t>() : nullptr;
+  pa.aff_scratch = search == kSearchThread ? W->aff.as<long long>() : nullptr;
   pa.budget = budget;
   pa.dump_limit = dump_limit;
   const int idle_pct = (opt.idle_percent > 0 && opt.idle_percent <= 100) ? opt.idle_percent : 50;
-  pa.idle_limit = std::max<unsigned long long>(1, (unsigned long long)n_warps * idle_pct / 100);
+  pa.idle_limit = std::max<unsigned long long>(1, (unsigned long long)n_searches * idle_pct / 100);
   const bool trace = getenv("WPM_TRACE") != nullptr;
+  pa.trace = trace ? 1 : 0;
   if (trace)
-    fprintf(stderr, "[wpm] %d instances, class %d (mw %d nw %d), %d blocks x %d threads, budget %lld, "
-            "ring %llu items of %d words, max depth %d\n", n_valid, k, size_class(k).mw,
-            size_class(k).nw, blocks, tpb, budget, ring_cap, iw, max_depth);
+    fprintf(stderr, "[wpm] %d instances, class %d (mw %d nw %d), %s search, %d blocks x %d "
+            "threads, budget %lld, ring %llu items of %d words, max depth %d\n", n_valid, k,
+            size_class(k).mw, size_class(k).nw, search == kSearchThread ? "thread" : "warp",
+            blocks, tpb, budget, ring_cap, iw, max_depth);
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   if (trace) {
     cudaEventCreate(&ev0);
@@ -468,7 +485,7 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
     hq->nodes = 0;
     CUDA_TRY(cudaMemcpyAsync(W->q.p, hq, sizeof(QueueCtl), cudaMemcpyHostToDevice, s));
     if (trace) cudaEventRecord(ev0, s);
-    CUDA_TRY(launch_expand(k, pa, (int)live, tpb, s));
+    CUDA_TRY(launch_expand(k, pa, (int)live, 256, s));
     if (trace) cudaEventRecord(ev1, s);
     CUDA_TRY(cudaMemcpyAsync(hq, W->q.p, sizeof(QueueCtl), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
@@ -490,9 +507,10 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
     hq->err = 0;
     hq->idle = 0;
     hq->nodes = 0;
+    hq->iters = hq->lanes_step = hq->lanes_fetch = hq->lanes_dump = hq->lanes_stopped = 0;
     CUDA_TRY(cudaMemcpyAsync(W->q.p, hq, sizeof(QueueCtl), cudaMemcpyHostToDevice, s));
     if (trace) cudaEventRecord(ev0, s);
-    CUDA_TRY(launch_dfs(k, pa, blocks, tpb, s));
+    CUDA_TRY(launch_dfs(k, search, pa, blocks, tpb, s));
     if (trace) cudaEventRecord(ev1, s);
     CUDA_TRY(cudaMemcpyAsync(hq, W->q.p, sizeof(QueueCtl), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
@@ -501,9 +519,15 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
     if (trace) {
       float ms = 0;
       cudaEventElapsedTime(&ms, ev0, ev1);
-      fprintf(stderr, "[wpm] dfs %d: %llu items, %llu taken, %llu new, %llu nodes, %.3f ms\n",
+      fprintf(stderr, "[wpm] dfs %d: %llu items, %llu taken, %llu new, %llu nodes, %.3f ms",
               pass_no++, tail - head, std::min(hq->head, tail) - head, hq->tail - tail, hq->nodes,
               ms);
+      if (hq->iters)
+        fprintf(stderr, "; warp iterations %llu, lanes/iteration: step %.2f fetch %.3f stopped "
+                "%.2f; dumps %llu", hq->iters, (double)hq->lanes_step / hq->iters,
+                (double)hq->lanes_fetch / hq->iters, (double)hq->lanes_stopped / hq->iters,
+                hq->lanes_dump);
+      fprintf(stderr, "\n");
     }
     head = std::min(hq->head, tail);
     tail = hq->tail;
@@ -629,6 +653,7 @@ static RunOptions options_from(const wpm_tuning *t, int mode) {
     o.frontier_target = t->frontier_target;
     o.ring_items = t->ring_items;
     o.idle_percent = t->idle_percent;
+    o.search = t->search;
   }
   return o;
 }

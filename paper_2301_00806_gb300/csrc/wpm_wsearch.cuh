@@ -1,5 +1,7 @@
-// wpm_search.cuh -- the search kernels of libwpm (included by wpm_class.cu, which is
-// compiled once per kernel size class).
+// wpm_wsearch.cuh -- the warp-per-search kernels of libwpm (included by wpm_class.cu, which is
+// compiled once per kernel size class). Used for the breadth-first expansion always, and for
+// the depth-first passes of large instances, whose per-thread state would not fit enough
+// searches per SM (wpm_tsearch.cuh has the per-thread search).
 //
 // One search per warp. The 32 lanes share one search state in shared memory and work
 // together on each node: every candidate child of a node is checked at once (one lane per
@@ -36,7 +38,7 @@ namespace wpm {
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
 template <int MW_, int NW_>
-struct Cls {
+struct WCls {
   static constexpr int MW = MW_, NW = NW_;
   static constexpr int AFF = (NW + 2 * MW + 1) & ~1;  // affine sums (8-byte aligned)
   static constexpr int SMW = AFF + 4 * kMaxAffine;    // state words per warp (even)
@@ -477,7 +479,7 @@ struct WSearch {
 // ------------------------------------------------------------------------------------
 
 template <class K>
-__global__ void __launch_bounds__(256) expand_kernel(PassArgs a, int n_items) {
+__global__ void __launch_bounds__(256) wexpand_kernel(PassArgs a, int n_items) {
   extern __shared__ uint32_t smem[];
   const int wib = threadIdx.x >> 5;
   const int i = blockIdx.x * (blockDim.x >> 5) + wib;
@@ -509,7 +511,7 @@ __global__ void __launch_bounds__(256) expand_kernel(PassArgs a, int n_items) {
 // ------------------------------------------------------------------------------------
 
 template <class K>
-__global__ void __launch_bounds__(256) dfs_kernel(PassArgs a) {
+__global__ void __launch_bounds__(256) wdfs_kernel(PassArgs a) {
   extern __shared__ uint32_t smem[];
   const int wib = threadIdx.x >> 5;
   WSearch<K> S;
@@ -588,20 +590,17 @@ __global__ void __launch_bounds__(256) dfs_kernel(PassArgs a) {
   }
 }
 
-// Launch modes of a size class.
-enum { kLaunchExpand = 0, kLaunchDfs = 1 };
-
 template <int MW, int NW>
-static cudaError_t launch_t(int mode, const PassArgs &a, int grid, int n_items, int tpb,
-                            size_t smem, cudaStream_t s) {
-  using K = Cls<MW, NW>;
-  if (mode == kLaunchExpand) {
-    auto fn = expand_kernel<K>;
+static cudaError_t wlaunch_t(int mode, const PassArgs &a, int grid, int n_items, int tpb,
+                             size_t smem, cudaStream_t s) {
+  using K = WCls<MW, NW>;
+  if (mode == 0) {
+    auto fn = wexpand_kernel<K>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     fn<<<grid, tpb, smem, s>>>(a, n_items);
   } else {
-    auto fn = dfs_kernel<K>;
+    auto fn = wdfs_kernel<K>;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     fn<<<grid, tpb, smem, s>>>(a);
@@ -610,9 +609,8 @@ static cudaError_t launch_t(int mode, const PassArgs &a, int grid, int n_items, 
 }
 
 template <int MW, int NW>
-static int occupancy_t(int tpb, size_t smem) {
-  using K = Cls<MW, NW>;
-  auto fn = dfs_kernel<K>;
+static int woccupancy_t(int tpb, size_t smem) {
+  auto fn = wdfs_kernel<WCls<MW, NW>>;
   if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
@@ -624,6 +622,5 @@ static int occupancy_t(int tpb, size_t smem) {
   }
   return blocks;
 }
-
 
 }  // namespace wpm

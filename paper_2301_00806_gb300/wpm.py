@@ -68,7 +68,7 @@ class Instance(C.Structure):
 class Tuning(C.Structure):
     _fields_ = [("frontier_target", C.c_int32), ("budget", C.c_int32),
                 ("threads_per_block", C.c_int32), ("idle_percent", C.c_int32),
-                ("ring_items", C.c_int64)]
+                ("ring_items", C.c_int64), ("search", C.c_int32), ("reserved", C.c_int32)]
 
 
 class EngineConfig(C.Structure):

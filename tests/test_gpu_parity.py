@@ -138,8 +138,13 @@ def _mixed(count=48, seed=11):
                                     {"budget": 7, "frontier_target": 1},
                                     {"budget": 64, "frontier_target": 100000},
                                     {"budget": 3, "ring_items": 3000, "threads_per_block": 64},
-                                    {"budget": 1000000, "frontier_target": 1, "threads_per_block": 256}],
-                         ids=["default", "budget1", "nofrontier", "wide", "smallring", "nobudget"])
+                                    {"budget": 1000000, "frontier_target": 1, "threads_per_block": 256},
+                                    {"search": 1, "budget": 2, "frontier_target": 1},
+                                    {"search": 2},
+                                    {"search": 2, "budget": 1, "frontier_target": 1},
+                                    {"search": 2, "budget": 5, "idle_percent": 100, "threads_per_block": 64}],
+                         ids=["default", "budget1", "nofrontier", "wide", "smallring", "nobudget",
+                              "thread_budget2", "warp", "warp_budget1", "warp_small"])
 def test_mixed_batch_with_tunings(W, tuning):
     insts = _mixed()
     orc = [oracle_run(inst, cap=-2)[1] for inst in insts]
