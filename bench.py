@@ -1,0 +1,338 @@
+"""Benchmark: batched enumeration of weak pseudo-manifolds on one GB300 (or N, weak scaling).
+
+Workload (default): 4096 seeded Picard-4 instances, n uniform in {3..8}, dual maps with
+m = n + 4 distinct nonzero rows of rank 4, property = the upper-bound-theorem cap; every
+instance's full sorted list of WPM facet masks. One step = one batched run of the whole
+path (candidate facets, ridges, search, per-instance sort) over the 4096 instances.
+
+  value  search nodes/s of the whole job, outputs kept on the device, timed with CUDA
+         events on the run's stream (inputs are host-side maps of 64 bytes each; the
+         library copies their descriptors in the same step)
+  e2e    the same metric through the C ABI with host buffers: the step includes copying
+         the inputs in and every sorted mask list out to pinned host memory
+
+--impl reference times the CPU oracle (the test oracle, unmodified) on a bounded sample of
+the same workload. Under torchrun each rank runs its own seeded 4096-instance batch (weak
+scaling, no collective on the data path); rank 0 prints the JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "search nodes/sec (batched, 4096 Picard-4 instances n=3..8)"
+UNIT = "nodes/s"
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle (reference arm and cpu_baseline): a spawn pool over sampled instances
+# ------------------------------------------------------------------------------------------
+
+def _oracle_job(args):
+    kind, n, m, cols = args
+    import oracle as O
+    f = O.candidate_facets(kind, n, m, cols)
+    c, nodes, probes, _ = O.enumerate_dfs(n, m, f, cap=O.CAP_UBT, list_mode=True, capacity=1 << 16)
+    return c, nodes, probes
+
+
+def oracle_sample(insts, stride):
+    """Every stride-th instance of the batch (a bounded, deterministic sample)."""
+    return [i for k, i in enumerate(insts) if k % stride == 0]
+
+
+def time_oracle(sample, cores):
+    import oracle as O
+    O.oracle.build()
+    ctx = mp.get_context("spawn")
+    # longest first (the search grows about 5x per unit of n), so the pool stays busy
+    jobs = sorted(((i.kind, i.n, i.m, list(i.cols)) for i in sample), key=lambda j: -j[1])
+    t0 = time.perf_counter()
+    with ctx.Pool(cores) as pool:
+        res = list(pool.imap_unordered(_oracle_job, jobs, chunksize=1))
+    dt = time.perf_counter() - t0
+    return sum(r[1] for r in res), dt, res
+
+
+# ------------------------------------------------------------------------------------------
+# clocks
+# ------------------------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int, path: str):
+        self.path = path
+        self.proc = None
+        self.index = index
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}",
+                                          f"--query-gpu={self.QUERY}", "--format=csv,noheader",
+                                          "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        try:
+            rows = [l.strip().split(", ") for l in open(self.path) if l.strip()]
+        except Exception:
+            rows = []
+        mhz, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                mhz.append(float(r[1].split()[0]))
+                mx = float(r[2].split()[0])
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip() == "Active":
+                        reasons.add(nm)
+            except Exception:
+                continue
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(mhz)}
+
+
+# ------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------
+
+def algorithmic_ops(res, insts):
+    """Integer operations the canonical tree requires (the roofline's numerator): each tried
+    child (node or probe) tests its n ridge counters (load, shift, test: 3 ops each), and each
+    accepted child updates its n counters on entry and on exit (load, add, store: 6 ops)."""
+    return sum(3 * i.n * (r.nodes + r.probes) + 6 * i.n * r.nodes for r, i in zip(res, insts))
+
+
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+    from paper_2301_00806_gb300 import instances as I, wpm
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", dev))
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    insts = I.batch_duals(args.count, 3, 8, seed=args.seed + rank)
+    specs = [wpm.BatchSpec("dual", i.n, i.m, i.cols, cap=wpm.CAP_UBT) for i in insts]
+    tuning = {"profile": 1}
+    stream = torch.cuda.Stream()
+
+    # counts first (untimed): they size the output lists
+    res = wpm.enumerate_batch(specs, list_mode=False, tuning=tuning, stream=stream)
+    caps = [max(1, r.count) for r in res]
+    words = [r.words for r in res]
+    offs = np.concatenate([[0], np.cumsum([c * w for c, w in zip(caps, words)])])
+    dev_buf = torch.empty(int(offs[-1]), dtype=torch.int64, device="cuda")
+    dev_out = [dev_buf[int(offs[k]):int(offs[k + 1])] for k in range(len(specs))]
+    nodes_step = sum(r.nodes for r in res)
+    ops_step = algorithmic_ops(res, insts)
+
+    def step_device():
+        return wpm.enumerate_batch(specs, list_mode=True, capacities=caps, tuning=tuning,
+                                   stream=stream, device_out=dev_out)
+
+    for _ in range(args.warmup):
+        step_device()
+    torch.cuda.synchronize()
+    clock = ClockSampler(dev, os.path.join(args.out_dir, f"clocks_rank{rank}.csv"))
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    dfs_ms = 0.0
+    dfs_launches = 0
+    launches = 0
+    with clock:
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            out = step_device()
+            st = wpm.last_run_stats()
+            dfs_ms += st["dfs_ms"]
+            dfs_launches += st["dfs_passes"]
+            launches += st["kernel_launches"]
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    assert all(r.status == 0 for r in out)
+    assert sum(r.nodes for r in out) == nodes_step
+
+    # end to end through the C ABI with host buffers (inputs in, sorted lists out)
+    host_caps = caps
+    e2e_times, h2d, d2h = [], 0, 0
+    for k in range(max(1, args.e2e_steps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out_h = wpm.enumerate_batch(specs, list_mode=True, capacities=host_caps, tuning=None,
+                                    stream=stream, words=words)
+        e2e_times.append(time.perf_counter() - t0)
+        st = wpm.last_run_stats()
+        h2d, d2h = st["h2d_bytes"], st["d2h_bytes"]
+    assert sum(r.nodes for r in out_h) == nodes_step
+
+    # the plain path: one instance per call, on a sample of the same batch
+    plain = None
+    if args.plain_sample > 0:
+        stride = max(1, len(insts) // args.plain_sample)
+        smp = [(s, i) for k, (s, i) in enumerate(zip(specs, insts)) if k % stride == 0]
+        pn = 0
+        t0 = time.perf_counter()
+        for s, i in smp:
+            r = wpm.enumerate(s.kind, s.n, s.m, s.cols, cap=s.cap, list_mode=False)
+            pn += r.nodes
+        pdt = time.perf_counter() - t0
+        plain = {"value": pn / pdt, "unit": UNIT, "instances": len(smp),
+                 "instances_per_s": len(smp) / pdt, "mode": "one wpm_enumerate call per instance"}
+
+    t = torch.tensor([ms, nodes_step * args.steps, float(launches)], dtype=torch.float64,
+                     device="cuda")
+    if world > 1:
+        import torch.distributed as dist
+        mx = t.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = t.clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        ms_all, nodes_all = float(mx[0]), float(sm[1])
+    else:
+        ms_all, nodes_all = ms, float(nodes_step * args.steps)
+    if rank != 0:
+        return None
+    clocks = clock.summary()
+    sec = ms_all / 1000.0
+    value = nodes_all / sec
+    inst_per_s = world * len(insts) * args.steps / sec
+    e2e_t = statistics.median(e2e_times)
+    from paper_2301_00806_gb300 import instances as _I  # noqa: F401
+    peak_mhz = 2070.0
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_ops = n_sm * 128 * peak_mhz * 1e6
+    achieved = ops_step * args.steps / (dfs_ms / 1000.0) if dfs_ms > 0 else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_all / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic (seeded dual maps; no dataset)",
+        "config": {"workload": f"{args.count} Picard-4 dual maps, n~U{{3..8}}, m=n+4, UBT cap, "
+                               f"full sorted WPM lists", "instances_per_gpu": args.count,
+                   "seed": args.seed, "mode": "list", "parallelism": f"replicas x{world}",
+                   "l2": "not flushed: each step streams GBs (work ring, output lists) through "
+                         "the 129 MB L2"},
+        "instances_per_s": inst_per_s,
+        "nodes_per_step": nodes_step * world,
+        "e2e": {"value": world * nodes_step / e2e_t, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_t * 1000.0},
+        "plain_launch": plain,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "int ops/s",
+                     "frac": (achieved / peak_ops) if achieved else None, "traffic": None,
+                     "kernel": "depth-first pass (tdfs_kernel)",
+                     "dfs_launches_per_step": dfs_launches / args.steps,
+                     "dfs_ms_per_step": dfs_ms / args.steps,
+                     "peak_from": f"{n_sm} SMs x 128 INT32 lanes x {peak_mhz:.0f} MHz (max clock)"},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    return line
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--count", type=int, default=4096)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--plain-sample", type=int, default=256)
+    ap.add_argument("--cpu-stride", type=int, default=64, help="oracle sample: every k-th instance")
+    ap.add_argument("--out-dir", default=os.path.join(ROOT, "gpurun_out"))
+    args = ap.parse_args()
+    os.makedirs(args.out_dir, exist_ok=True)
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+
+    from paper_2301_00806_gb300 import instances as I
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        insts = I.batch_duals(args.count, 3, 8, seed=args.seed)
+        sample = oracle_sample(insts, args.cpu_stride)
+        per_step = []
+        total_nodes = 0
+        for _ in range(args.warmup):
+            time_oracle(sample[:2], cores)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            nodes, dt, _ = time_oracle(sample, cores)
+            per_step.append(dt)
+            total_nodes += nodes
+        wall = time.perf_counter() - t0
+        value = total_nodes / wall
+        desc = f"every {args.cpu_stride}th of the {args.count} instances ({len(sample)} maps)"
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * wall / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8/int",
+            "data": "synthetic (seeded dual maps)",
+            "config": {"workload": f"{args.count} Picard-4 dual maps, n~U{{3..8}}, UBT cap "
+                                   f"(oracle on a sample)", "seed": args.seed},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+        }), flush=True)
+        return
+
+    # CPU baseline first (spawn pool, before any CUDA call), rank 0 at N=1 only
+    cpu = None
+    if rank == 0 and world == 1 and args.cpu_stride > 0:
+        insts = I.batch_duals(args.count, 3, 8, seed=args.seed)
+        sample = oracle_sample(insts, args.cpu_stride)
+        nodes, dt, _ = time_oracle(sample, cores)
+        cpu = {"value": nodes / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"every {args.cpu_stride}th of the {args.count} instances "
+                         f"({len(sample)} maps, {nodes} nodes, {dt:.1f} s)"}
+    line = run_ours(args, rank, world)
+    if line is not None:
+        line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -136,12 +136,32 @@ typedef struct {
     int32_t budget;
     int32_t threads_per_block;
     int32_t idle_percent;   /* a depth-first pass ends (busy searches return their work to
-                               the ring) once this percentage of searches is idle; 0 = 50 */
+                               the ring) once this percentage of searches is idle; 0 = 20 */
     int64_t ring_items;
     int32_t search;         /* 1: one search per thread, 2: one search per warp, 0: by size
                                (per thread up to n = 9)                                    */
-    int32_t reserved;
+    int32_t profile;        /* nonzero: time every depth-first pass with CUDA events on the
+                               run's stream (see wpm_last_run_stats)                       */
 } wpm_tuning;
+
+/* Statistics of the calling thread's last enumeration run. */
+typedef struct {
+    uint64_t kernel_launches;  /* kernels the run launched (setup, roots, passes, sort, copy)  */
+    uint64_t expand_passes;    /* breadth-first passes                                         */
+    uint64_t dfs_passes;       /* depth-first passes                                           */
+    uint64_t sort_passes;      /* merge passes of the output sort                              */
+    uint64_t items;            /* work items taken by the depth-first passes                   */
+    double dfs_ms;             /* summed duration of the depth-first passes (profile only)     */
+    double expand_ms;          /* summed duration of the expansion passes (profile only)      */
+    int32_t search;            /* search mode used (1 thread, 2 warp)                          */
+    int32_t size_class;        /* kernel size class                                            */
+    int32_t searches;          /* concurrent searches of a depth-first pass                    */
+    int32_t reserved;
+    uint64_t h2d_bytes;        /* bytes copied host -> device by the run                       */
+    uint64_t d2h_bytes;        /* bytes copied device -> host by the run                       */
+} wpm_run_stats;
+
+int wpm_last_run_stats(wpm_run_stats *out);
 
 /*
  * The candidate facets of a map (Section 3.1; Proposition 4.2), in lexicographic order,

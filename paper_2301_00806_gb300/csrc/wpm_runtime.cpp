@@ -28,6 +28,7 @@
 namespace wpm {
 
 static thread_local std::string t_err;
+static thread_local wpm_run_stats t_stats;
 
 static int fail(int code, const char *fmt, ...) {
   char buf[512];
@@ -103,6 +104,7 @@ struct Workspace {
   int device = -1;
   int sms = 0;
   cudaStream_t own = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   DevBuf inst, outd, ctr, arena, cond, ids, q, ring, stack, aff, out, seg, segs, stage;
   PinBuf h_inst, h_outd, h_q, h_ctr, h_cond, h_ids, h_seg, h_segs, h_stage;
   void release() {
@@ -242,10 +244,17 @@ struct RunOptions {
   long long ring_items = 0;
   int idle_percent = 0;
   int search = 0;
+  bool profile = false;
   bool setup_only = false;  // stop after the setup kernel (candidate facets)
 };
 
 static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Account a host <-> device copy of the current run: (dst, src, bytes) as passed to the copy.
+static void count_copy(const void *, const void *, size_t bytes, cudaMemcpyKind kind) {
+  if (kind == cudaMemcpyHostToDevice) t_stats.h2d_bytes += bytes;
+  else if (kind == cudaMemcpyDeviceToHost) t_stats.d2h_bytes += bytes;
+}
 
 // The engine of every entry point: run the instances `hi` on stream `s`.
 // outs[i] (optional) provides list-mode buffers; res[i] receives the outcome.
@@ -253,6 +262,7 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
                const wpm_output *outs, std::vector<InstResult> &res, std::vector<uint16_t> *facets_out) {
   const int n_inst = (int)hi.size();
   res.assign(n_inst, InstResult());
+  memset(&t_stats, 0, sizeof(t_stats));
   if (n_inst == 0) return WPM_OK;
 
   // ---- device layout of the tables and of the caller's conditions --------------------
@@ -315,9 +325,13 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
     d.n_given = (int)h.given.size();
   }
   if (cond) CUDA_TRY(cudaMemcpyAsync(W->cond.p, W->h_cond.p, cond, cudaMemcpyHostToDevice, s));
+  count_copy(W->cond.p, W->h_cond.p, cond, cudaMemcpyHostToDevice);
   CUDA_TRY(cudaMemcpyAsync(W->inst.p, hd, sizeof(InstDesc) * n_inst, cudaMemcpyHostToDevice, s));
+  count_copy(W->inst.p, hd, sizeof(InstDesc) * n_inst, cudaMemcpyHostToDevice);
   CUDA_TRY(launch_setup(W->inst.as<InstDesc>(), n_inst, s));
+  t_stats.kernel_launches++;
   CUDA_TRY(cudaMemcpyAsync(hd, W->inst.p, sizeof(InstDesc) * n_inst, cudaMemcpyDeviceToHost, s));
+  count_copy(hd, W->inst.p, sizeof(InstDesc) * n_inst, cudaMemcpyDeviceToHost);
   CUDA_TRY(cudaStreamSynchronize(s));
 
   // ---- per-instance checks ----------------------------------------------------------
@@ -427,17 +441,22 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
     }
   }
   CUDA_TRY(cudaMemcpyAsync(W->outd.p, ho, sizeof(OutDesc) * n_inst, cudaMemcpyHostToDevice, s));
+  count_copy(W->outd.p, ho, sizeof(OutDesc) * n_inst, cudaMemcpyHostToDevice);
   CUDA_TRY(cudaMemsetAsync(W->ctr.p, 0, 8ull * kCtrN * n_inst, s));
   int32_t *hids = W->h_ids.as<int32_t>();
   for (int j = 0; j < n_valid; j++) hids[j] = valid[j];
   CUDA_TRY(cudaMemcpyAsync(W->ids.p, hids, 4ull * n_valid, cudaMemcpyHostToDevice, s));
+  count_copy(W->ids.p, hids, 4ull * n_valid, cudaMemcpyHostToDevice);
   QueueCtl *hq = W->h_q.as<QueueCtl>();
   memset(hq, 0, sizeof(QueueCtl));
   CUDA_TRY(cudaMemcpyAsync(W->q.p, hq, sizeof(QueueCtl), cudaMemcpyHostToDevice, s));
+  count_copy(W->q.p, hq, sizeof(QueueCtl), cudaMemcpyHostToDevice);
+  t_stats.kernel_launches++;
   CUDA_TRY(launch_roots(W->inst.as<InstDesc>(), n_valid, W->ids.as<int32_t>(),
                         W->ctr.as<unsigned long long>(), W->ring.as<uint32_t>(), ring_cap, iw,
                         size_class(k).mw, W->q.as<QueueCtl>(), s));
   CUDA_TRY(cudaMemcpyAsync(hq, W->q.p, sizeof(QueueCtl), cudaMemcpyDeviceToHost, s));
+  count_copy(hq, W->q.p, sizeof(QueueCtl), cudaMemcpyDeviceToHost);
   CUDA_TRY(cudaStreamSynchronize(s));
 
   PassArgs pa;
@@ -454,7 +473,7 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
   pa.aff_scratch = search == kSearchThread ? W->aff.as<long long>() : nullptr;
   pa.budget = budget;
   pa.dump_limit = dump_limit;
-  const int idle_pct = (opt.idle_percent > 0 && opt.idle_percent <= 100) ? opt.idle_percent : 50;
+  const int idle_pct = (opt.idle_percent > 0 && opt.idle_percent <= 100) ? opt.idle_percent : 20;
   pa.idle_limit = std::max<unsigned long long>(1, (unsigned long long)n_searches * idle_pct / 100);
   const bool trace = getenv("WPM_TRACE") != nullptr;
   pa.trace = trace ? 1 : 0;
@@ -463,11 +482,15 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
             "threads, budget %lld, ring %llu items of %d words, max depth %d\n", n_valid, k,
             size_class(k).mw, size_class(k).nw, search == kSearchThread ? "thread" : "warp",
             blocks, tpb, budget, ring_cap, iw, max_depth);
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  if (trace) {
-    cudaEventCreate(&ev0);
-    cudaEventCreate(&ev1);
+  t_stats.search = search;
+  t_stats.size_class = k;
+  t_stats.searches = n_searches;
+  const bool timed = trace || opt.profile;
+  if (timed && !W->ev0) {
+    CUDA_TRY(cudaEventCreate(&W->ev0));
+    CUDA_TRY(cudaEventCreate(&W->ev1));
   }
+  cudaEvent_t ev0 = W->ev0, ev1 = W->ev1;
   int pass_no = 0;
 
   // ---- breadth-first expansion, then depth-first passes -----------------------------
@@ -484,15 +507,22 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
     hq->idle = 0;
     hq->nodes = 0;
     CUDA_TRY(cudaMemcpyAsync(W->q.p, hq, sizeof(QueueCtl), cudaMemcpyHostToDevice, s));
-    if (trace) cudaEventRecord(ev0, s);
+  count_copy(W->q.p, hq, sizeof(QueueCtl), cudaMemcpyHostToDevice);
+    if (timed) CUDA_TRY(cudaEventRecord(ev0, s));
     CUDA_TRY(launch_expand(k, pa, (int)live, 256, s));
-    if (trace) cudaEventRecord(ev1, s);
+    if (timed) CUDA_TRY(cudaEventRecord(ev1, s));
+    t_stats.kernel_launches++;
+    t_stats.expand_passes++;
     CUDA_TRY(cudaMemcpyAsync(hq, W->q.p, sizeof(QueueCtl), cudaMemcpyDeviceToHost, s));
+  count_copy(hq, W->q.p, sizeof(QueueCtl), cudaMemcpyDeviceToHost);
     CUDA_TRY(cudaStreamSynchronize(s));
     if (hq->err) return fail(WPM_ERR_NOMEM, "work ring overflow during expansion");
+    float ms = 0;
+    if (timed) {
+      CUDA_TRY(cudaEventElapsedTime(&ms, ev0, ev1));
+      t_stats.expand_ms += ms;
+    }
     if (trace) {
-      float ms = 0;
-      cudaEventElapsedTime(&ms, ev0, ev1);
       fprintf(stderr, "[wpm] expand %d: %llu items -> %llu items, %.3f ms\n", pass_no++, live,
               hq->tail - tail, ms);
     }
@@ -509,16 +539,24 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
     hq->nodes = 0;
     hq->iters = hq->lanes_step = hq->lanes_fetch = hq->lanes_dump = hq->lanes_stopped = 0;
     CUDA_TRY(cudaMemcpyAsync(W->q.p, hq, sizeof(QueueCtl), cudaMemcpyHostToDevice, s));
-    if (trace) cudaEventRecord(ev0, s);
+  count_copy(W->q.p, hq, sizeof(QueueCtl), cudaMemcpyHostToDevice);
+    if (timed) CUDA_TRY(cudaEventRecord(ev0, s));
     CUDA_TRY(launch_dfs(k, search, pa, blocks, tpb, s));
-    if (trace) cudaEventRecord(ev1, s);
+    if (timed) CUDA_TRY(cudaEventRecord(ev1, s));
+    t_stats.kernel_launches++;
+    t_stats.dfs_passes++;
     CUDA_TRY(cudaMemcpyAsync(hq, W->q.p, sizeof(QueueCtl), cudaMemcpyDeviceToHost, s));
+  count_copy(hq, W->q.p, sizeof(QueueCtl), cudaMemcpyDeviceToHost);
     CUDA_TRY(cudaStreamSynchronize(s));
     if (hq->err & 1ull) return fail(WPM_ERR_NOMEM, "work ring overflow (raise ring_items)");
     if (hq->err & 2ull) return fail(WPM_ERR_LIMIT, "search stack overflow");
+    t_stats.items += std::min(hq->head, tail) - head;
+    float ms = 0;
+    if (timed) {
+      CUDA_TRY(cudaEventElapsedTime(&ms, ev0, ev1));
+      t_stats.dfs_ms += ms;
+    }
     if (trace) {
-      float ms = 0;
-      cudaEventElapsedTime(&ms, ev0, ev1);
       fprintf(stderr, "[wpm] dfs %d: %llu items, %llu taken, %llu new, %llu nodes, %.3f ms",
               pass_no++, tail - head, std::min(hq->head, tail) - head, hq->tail - tail, hq->nodes,
               ms);
@@ -536,6 +574,7 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
   // ---- counters ----------------------------------------------------------------------
   unsigned long long *hc2 = W->h_ctr.as<unsigned long long>();
   CUDA_TRY(cudaMemcpyAsync(hc2, W->ctr.p, 8ull * kCtrN * n_inst, cudaMemcpyDeviceToHost, s));
+  count_copy(hc2, W->ctr.p, 8ull * kCtrN * n_inst, cudaMemcpyDeviceToHost);
   CUDA_TRY(cudaStreamSynchronize(s));
   std::vector<int32_t> sorted_ids;
   std::vector<unsigned long long> seg(1, 0);
@@ -573,17 +612,24 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
   for (int j = 0; j < ns; j++) hsid[j] = sorted_ids[j];
   int32_t *d_sid = W->ids.as<int32_t>() + n_inst;
   CUDA_TRY(cudaMemcpyAsync(W->seg.p, hseg, 8ull * (ns + 1), cudaMemcpyHostToDevice, s));
+  count_copy(W->seg.p, hseg, 8ull * (ns + 1), cudaMemcpyHostToDevice);
   CUDA_TRY(cudaMemcpyAsync(d_sid, hsid, 4ull * ns, cudaMemcpyHostToDevice, s));
+  count_copy(d_sid, hsid, 4ull * ns, cudaMemcpyHostToDevice);
   const unsigned long long total = seg.back();
   int parity = 0;
   for (unsigned long long runlen = 1; runlen < max_len; runlen *= 2) {
     CUDA_TRY(launch_sort_pass(W->inst.as<InstDesc>(), W->outd.as<OutDesc>(), d_sid, ns,
                               W->seg.as<unsigned long long>(), total, runlen, parity, s));
+    t_stats.kernel_launches++;
+    t_stats.sort_passes++;
     parity ^= 1;
   }
-  if (parity)  // one copying pass brings the result back to `out`
+  if (parity) {  // one copying pass brings the result back to `out`
     CUDA_TRY(launch_sort_pass(W->inst.as<InstDesc>(), W->outd.as<OutDesc>(), d_sid, ns,
                               W->seg.as<unsigned long long>(), total, 1ull << 62, 1, s));
+    t_stats.kernel_launches++;
+    t_stats.sort_passes++;
+  }
 
   // ---- copy-out -------------------------------------------------------------------------
   std::vector<CopySeg> cs;
@@ -619,11 +665,13 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
   memcpy(W->h_segs.as<char>() + sizeof(CopySeg) * cs.size(), cp.data(), 8 * cp.size());
   CUDA_TRY(cudaMemcpyAsync(W->segs.p, W->h_segs.p, sizeof(CopySeg) * cs.size() + 8 * cp.size(),
                            cudaMemcpyHostToDevice, s));
+  t_stats.kernel_launches++;
   CUDA_TRY(launch_segment_copy(W->segs.as<CopySeg>(), (int)cs.size(),
                                (const unsigned long long *)(W->segs.as<char>() +
                                                             sizeof(CopySeg) * cs.size()),
                                cp.back(), s));
   if (sw) CUDA_TRY(cudaMemcpyAsync(W->h_stage.p, W->stage.p, 8 * sw, cudaMemcpyDeviceToHost, s));
+  count_copy(W->h_stage.p, W->stage.p, 8 * sw, cudaMemcpyDeviceToHost);
   CUDA_TRY(cudaStreamSynchronize(s));
   sw = 0;
   for (int i : host_ids) {
@@ -654,6 +702,7 @@ static RunOptions options_from(const wpm_tuning *t, int mode) {
     o.ring_items = t->ring_items;
     o.idle_percent = t->idle_percent;
     o.search = t->search;
+    o.profile = t->profile != 0;
   }
   return o;
 }
@@ -685,6 +734,12 @@ using namespace wpm;
 extern "C" {
 
 const char *wpm_last_error(void) { return t_err.c_str(); }
+
+int wpm_last_run_stats(wpm_run_stats *out) {
+  if (!out) return fail(WPM_ERR_INPUT, "out is NULL");
+  *out = t_stats;
+  return WPM_OK;
+}
 
 int wpm_version(void) { return 1; }
 

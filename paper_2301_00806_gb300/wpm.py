@@ -68,7 +68,15 @@ class Instance(C.Structure):
 class Tuning(C.Structure):
     _fields_ = [("frontier_target", C.c_int32), ("budget", C.c_int32),
                 ("threads_per_block", C.c_int32), ("idle_percent", C.c_int32),
-                ("ring_items", C.c_int64), ("search", C.c_int32), ("reserved", C.c_int32)]
+                ("ring_items", C.c_int64), ("search", C.c_int32), ("profile", C.c_int32)]
+
+
+class RunStats(C.Structure):
+    _fields_ = [("kernel_launches", C.c_uint64), ("expand_passes", C.c_uint64),
+                ("dfs_passes", C.c_uint64), ("sort_passes", C.c_uint64), ("items", C.c_uint64),
+                ("dfs_ms", C.c_double), ("expand_ms", C.c_double), ("search", C.c_int32),
+                ("size_class", C.c_int32), ("searches", C.c_int32), ("reserved", C.c_int32),
+                ("h2d_bytes", C.c_uint64), ("d2h_bytes", C.c_uint64)]
 
 
 class EngineConfig(C.Structure):
@@ -100,6 +108,7 @@ def lib():
             L.wpm_enumerate_batch.argtypes = [C.POINTER(Instance), C.c_int, C.POINTER(Output),
                                               C.c_int, C.POINTER(Tuning), C.c_void_p]
             L.wpm_last_error.restype = C.c_char_p
+            L.wpm_last_run_stats.argtypes = [C.POINTER(RunStats)]
             L.wpm_release_workspace.argtypes = []
             if not hasattr(L, "wpm_engine_create"):
                 _lib = L
@@ -252,13 +261,14 @@ class BatchSpec:
 
 
 def enumerate_batch(specs: List[BatchSpec], list_mode=True, capacities=None, tuning=None,
-                    stream=None, device_out=None) -> List[Result]:
+                    stream=None, device_out=None, words=None) -> List[Result]:
     """wpm_enumerate_batch over many maps in one batched GPU run.
 
     capacities: per-instance mask capacity (list mode). device_out: optional list of torch
     CUDA uint64 tensors (one per instance, capacity x W) to receive the masks on the device;
     then Result.masks is None and the tensors hold the sorted masks. stream: a torch CUDA
-    stream (or raw cudaStream_t int)."""
+    stream (or raw cudaStream_t int). words: per-instance words per mask (ceil(M/64), e.g.
+    from a counting run) to size host buffers exactly; default 16 (the widest)."""
     n = len(specs)
     keep = _Keep()
     insts = (Instance * max(n, 1))()
@@ -285,7 +295,8 @@ def enumerate_batch(specs: List[BatchSpec], list_mode=True, capacities=None, tun
                 outs[i].capacity = cap
                 bufs.append(None)
             else:
-                buf = np.zeros(max(cap, 1) * 16, dtype=np.uint64)
+                w = int(words[i]) if words is not None else 16
+                buf = np.empty(max(cap, 1) * w, dtype=np.uint64)
                 bufs.append(buf)
                 outs[i].masks = _p(buf, C.c_uint64)
                 outs[i].capacity = cap
@@ -313,6 +324,15 @@ def enumerate_batch(specs: List[BatchSpec], list_mode=True, capacities=None, tun
             masks = bufs[i][: int(o.count) * w].reshape(int(o.count), w).copy()
         res.append(_result(o, masks))
     return res
+
+
+def last_run_stats() -> dict:
+    """Statistics of this thread's last run (kernel launches, passes, pass durations)."""
+    st = RunStats()
+    r = lib().wpm_last_run_stats(C.byref(st))
+    if r != OK:
+        raise _err(r)
+    return {f: getattr(st, f) for f, _ in RunStats._fields_ if f != "reserved"}
 
 
 def release_workspace() -> None:
