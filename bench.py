@@ -277,7 +277,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--plain-sample", type=int, default=256)
     ap.add_argument("--cpu-stride", type=int, default=64, help="oracle sample: every k-th instance")
-    ap.add_argument("--out-dir", default=os.path.join(ROOT, "gpurun_out"))
+    ap.add_argument("--out-dir", default=os.path.join(ROOT, "bench_out"),
+                    help="where the sampled clock log is written")
     args = ap.parse_args()
     os.makedirs(args.out_dir, exist_ok=True)
     rank = int(os.environ.get("RANK", 0))
