@@ -199,6 +199,20 @@ int wpm_enumerate_facets(const uint16_t *facets, int M, int n, int m,
 int wpm_enumerate_batch(const wpm_instance *inst, int count, wpm_output *outs, int mode,
                         const wpm_tuning *tuning, void *cuda_stream);
 
+/*
+ * wpm_candidate_facets with no allocation (the paper has no counterpart: this serves callers
+ * that must not allocate, e.g. a service that reserved its device memory at start-up, a host
+ * framework whose allocator owns the device, or code running while a stream is captured into
+ * a CUDA graph). Same inputs and output as wpm_candidate_facets (host pointers), run on
+ * `cuda_stream` (NULL: the default stream), which the call synchronises. Its device scratch
+ * is one fixed 512 KiB __device__ array of the library, present on every GPU that loads
+ * it; maps with C(m,n) + C(m,n-1) beyond about 7000 ranks are rejected with WPM_ERR_LIMIT.
+ * The first call on a device looks up that array's address (make it before any stream
+ * capture). Calls share the array: calls that overlap on the GPU race.
+ */
+int wpm_candidate_facets_static(const uint32_t *lambda_cols, int kind, int n, int m,
+                                uint16_t *facets_out, int cap, void *cuda_stream);
+
 /* ---- misc -------------------------------------------------------------------------- */
 const char *wpm_last_error(void);
 int wpm_version(void);

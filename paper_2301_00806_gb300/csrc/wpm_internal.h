@@ -147,6 +147,9 @@ cudaError_t launch_sort_pass(const InstDesc *d_inst, const OutDesc *d_outs, cons
                              int n_ids, const unsigned long long *d_seg, unsigned long long total,
                              unsigned long long run, int parity, cudaStream_t s);
 
+// Record the calling thread's last error (wpm_last_error) and return `code`.
+int set_last_error(int code, const char *msg);
+
 // Copy segment s: prefix[s+1] - prefix[s] words from src to dst (device pointers).
 struct CopySeg {
   const uint64_t *src;

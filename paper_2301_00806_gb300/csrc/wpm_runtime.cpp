@@ -40,6 +40,8 @@ static int fail(int code, const char *fmt, ...) {
   return code;
 }
 
+int set_last_error(int code, const char *msg) { return fail(code, "%s", msg); }
+
 #define CUDA_TRY(x)                                                                   \
   do {                                                                                \
     cudaError_t e_ = (x);                                                             \
