@@ -323,3 +323,39 @@ def test_outputs_are_wpms_n8(W):
         assert len(fac) <= I.ubt_cap(8)
     keys = [tuple(int(w) for w in reversed(r)) for r in g.masks]
     assert keys == sorted(keys) and len(set(keys)) == len(keys)
+
+
+# ---------------------------------------------------------------------------------------
+# Table 2 (first row) at the sizes the paper ran for hours and days per orbit
+# ---------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("row", [r for r in T2 if r[0] >= 8], ids=[f"n{r[0]}" for r in T2 if r[0] >= 8])
+@pytest.mark.parametrize("search", [1, 2], ids=["thread", "warp"])
+def test_table2_line7_large_n(W, row, search):
+    n, want = row
+    reps = I.idcm_orbit_reps(n)
+    specs = [W.BatchSpec("dual", n, n + 4, r, cap=-2, base_facet=True) for r in reps]
+    res = W.enumerate_batch(specs, list_mode=False, tuning={"search": search})
+    assert sum(r.count for r in res) == want
+
+
+@pytest.mark.parametrize("n", [9, 10])
+def test_table2_one_orbit_against_oracle(W, n):
+    rows = I.idcm_orbit_reps(n)[-1]
+    f = O.candidate_facets("dual", n, n + 4, rows)
+    c, nd, pr, _ = O.enumerate_dfs(n, n + 4, f, cap=-2, base_facet=True, list_mode=False)
+    g = W.enumerate("dual", n, n + 4, rows, cap=-2, base_facet=True, list_mode=False)
+    assert (g.count, g.nodes, g.probes) == (c, nd, pr)
+
+
+def test_n11_orbit_against_oracle(W):
+    """The one IDCM orbit of n = 11 (15 vertices, 840 candidate facets) with the base facet and
+    the cap: no count for it is printed in the paper (Table 2 stops at n = 10), so the oracle
+    is the check (about 66M search nodes on the host)."""
+    rows = I.idcm_orbit_reps(11)[0]
+    f = O.candidate_facets("dual", 11, 15, rows)
+    c, nd, pr, _ = O.enumerate_dfs(11, 15, f, cap=-2, base_facet=True, list_mode=False)
+    for search in (1, 2):
+        g = W.enumerate_batch([W.BatchSpec("dual", 11, 15, rows, cap=-2, base_facet=True)],
+                              list_mode=False, tuning={"search": search})[0]
+        assert (g.count, g.nodes, g.probes) == (c, nd, pr)
