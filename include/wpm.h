@@ -142,6 +142,10 @@ typedef struct {
                                (per thread up to n = 9)                                    */
     int32_t profile;        /* nonzero: time every depth-first pass with CUDA events on the
                                run's stream (see wpm_last_run_stats)                       */
+    int32_t time_limit_ms;  /* > 0: launch no depth-first pass after this much wall time;
+                               unfinished instances then report WPM_ERR_TIMEOUT with the
+                               counts reached so far (no masks)                            */
+    int32_t reserved;
 } wpm_tuning;
 
 /* Statistics of the calling thread's last enumeration run. */
@@ -212,6 +216,44 @@ int wpm_enumerate_batch(const wpm_instance *inst, int count, wpm_output *outs, i
  */
 int wpm_candidate_facets_static(const uint32_t *lambda_cols, int kind, int n, int m,
                                 uint16_t *facets_out, int cap, void *cuda_stream);
+
+/* ---- serving engine (continuous batching) ------------------------------------------ */
+/*
+ * Serving (continuous batching). An engine keeps a device work ring resident and runs search
+ * passes over every admitted job together (the per-map calls of Algorithm 4.4, Section 4.2,
+ * served as independent requests). A job is admitted, in arrival order, when a
+ * job slot is free and its output region (out_capacity masks, list mode) fits in the engine's
+ * output memory; jobs submitted while others run join at the next step and share the GPU with
+ * them. Results are identical to wpm_enumerate's. One engine is driven from one host thread.
+ */
+typedef struct wpm_engine wpm_engine;
+
+typedef struct {
+    int64_t memory_bytes;   /* device memory for job outputs; 0 = 8 GiB                   */
+    int32_t max_jobs;       /* concurrent jobs (slots); 0 = 1024                          */
+    int32_t budget;         /* most search nodes per search per step; 0 = 4096            */
+    int32_t max_n;          /* largest n admitted (sets the kernel size class and the
+                               search depth, the upper-bound cap of n); 0 = 11             */
+    int32_t reserved;
+} wpm_engine_config;
+
+/* Create an engine on the current device; stream may be NULL (the engine's own stream). */
+int wpm_engine_create(const wpm_engine_config *cfg, void *cuda_stream, wpm_engine **out);
+/* Queue a job (copied; pointers may be freed after the call). mode as above;
+ * out_capacity: masks to reserve in list mode. job_id receives a handle. */
+int wpm_engine_submit(wpm_engine *e, const wpm_instance *inst, int mode,
+                      uint64_t out_capacity, uint64_t *job_id);
+/* Admit what fits, run one search pass over everything resident, retire finished jobs.
+ * *n_active receives the jobs holding a slot afterwards. */
+int wpm_engine_step(wpm_engine *e, int *n_active);
+/* Finished jobs since the last poll: fills up to cap ids; returns how many. */
+int wpm_engine_poll(wpm_engine *e, uint64_t *job_ids, int cap);
+/* Copy a finished job's result into out (list mode: out->masks, a host buffer of
+ * out->capacity masks) and forget the job. WPM_ERR_CAPACITY keeps the result for a retry with
+ * a larger buffer; a job whose own out_capacity was too small reports WPM_ERR_CAPACITY with
+ * its count. */
+int wpm_engine_result(wpm_engine *e, uint64_t job_id, wpm_output *out);
+void wpm_engine_destroy(wpm_engine *e);
 
 /* ---- misc -------------------------------------------------------------------------- */
 const char *wpm_last_error(void);

@@ -521,6 +521,8 @@ typedef struct {
     int size;              /* |In|                                                    */
     sink_t *sink;
     uint64_t nodes, probes;
+    uint64_t max_nodes;    /* 0: no limit; otherwise stop (and report) beyond this many nodes */
+    int aborted;
 } dfs_t;
 
 /* Try to add facet p to In. Returns 1 and applies it when every check of the canonical
@@ -567,6 +569,7 @@ static void dfs_visit(dfs_t *d)
     const incidence_t *I = d->I;
     int M = I->M, N = I->N;
     d->nodes++;
+    if (d->max_nodes && d->nodes > d->max_nodes) { d->aborted = 1; return; }
     int r = -1;
     for (int i = 0; i < N; i++)
         if (d->deg[i] == 1) { r = i; break; }
@@ -589,6 +592,7 @@ static void dfs_visit(dfs_t *d)
             }
             for (int b = 0; b < nu; b++)
                 if (b != a) d->st[und[b]] = UNDECIDED;
+            if (d->aborted) return;
         }
         return;
     }
@@ -608,12 +612,32 @@ static void dfs_visit(dfs_t *d)
             d->probes++;
         }
         for (int b = 0; b < a; b++) d->st[und[b]] = UNDECIDED;
+        if (d->aborted) break;
     }
     free(und);
 }
 
+static int enumerate_dfs_budget(int n, int m, int M, const uint16_t *facets, const orc_cond *c,
+                                uint64_t *masks, uint64_t cap_masks, orc_stats *st,
+                                uint64_t max_nodes);
+
 int orc_enumerate_dfs(int n, int m, int M, const uint16_t *facets, const orc_cond *c,
                       uint64_t *masks, uint64_t cap_masks, orc_stats *st)
+{
+    return enumerate_dfs_budget(n, m, M, facets, c, masks, cap_masks, st, 0);
+}
+
+/* As orc_enumerate_dfs, but give up (returning ORC_ERR_BUDGET) after max_nodes nodes. */
+#define ORC_ERR_BUDGET -7
+int orc_enumerate_dfs_budget(int n, int m, int M, const uint16_t *facets, const orc_cond *c,
+                             orc_stats *st, uint64_t max_nodes)
+{
+    return enumerate_dfs_budget(n, m, M, facets, c, NULL, 0, st, max_nodes);
+}
+
+static int enumerate_dfs_budget(int n, int m, int M, const uint16_t *facets, const orc_cond *c,
+                                uint64_t *masks, uint64_t cap_masks, orc_stats *st,
+                                uint64_t max_nodes)
 {
     int cap = resolve_cap(c->cap, n, m);
     if (cap == -3) return ORC_ERR_INPUT;
@@ -623,7 +647,7 @@ int orc_enumerate_dfs(int n, int m, int M, const uint16_t *facets, const orc_con
     sink_t snk = { masks, cap_masks, 0, (M + 63) / 64, 0 };
     dfs_t d;
     memset(&d, 0, sizeof(d));
-    d.I = &I; d.c = c; d.cap = cap; d.sink = &snk;
+    d.I = &I; d.c = c; d.cap = cap; d.sink = &snk; d.max_nodes = max_nodes;
     int na = c->n_affine;
     d.posall = (long *)calloc(na ? na : 1, sizeof(long));
     d.negin = (long *)calloc(na ? na : 1, sizeof(long));
@@ -655,6 +679,99 @@ int orc_enumerate_dfs(int n, int m, int M, const uint16_t *facets, const orc_con
     incidence_free(&I);
     rc = sink_finish(&snk);
     if (st) { st->count = snk.count; st->nodes = d.nodes; st->probes = d.probes; }
+    if (d.aborted) return ORC_ERR_BUDGET;
+    return rc;
+}
+
+/* ---------------------------------------------------------------------------------- */
+/* A seeded random walk down the canonical tree, used to pick subtrees of a large        */
+/* instance as test inputs: from the root, `depth` times, list the children that pass     */
+/* their checks and step into one drawn uniformly (splitmix64, Steele-Lea-Flood 2014);    */
+/* at a node without children the walk starts again from the root with the generator     */
+/* continuing. The node reached is returned as its In and Out masks (Out including the    */
+/* facets excluded on the way), so that forced-in = In, forced-out = Out roots exactly    */
+/* that subtree.                                                                          */
+/* ---------------------------------------------------------------------------------- */
+
+static uint64_t splitmix64_next(uint64_t *state)
+{
+    uint64_t z = (*state += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+int orc_walk(int n, int m, int M, const uint16_t *facets, const orc_cond *c, uint64_t seed,
+             int depth, uint64_t *in_mask, uint64_t *out_mask)
+{
+    int cap = resolve_cap(c->cap, n, m);
+    if (cap == -3 || c->base_facet || c->forced_in || c->forced_out) return ORC_ERR_INPUT;
+    incidence_t I;
+    int rc = incidence_build(n, M, facets, &I);
+    if (rc) return rc;
+    dfs_t d;
+    memset(&d, 0, sizeof(d));
+    d.I = &I; d.c = c; d.cap = cap;
+    int na = c->n_affine;
+    d.posall = (long *)calloc(na ? na : 1, sizeof(long));
+    d.negin = (long *)calloc(na ? na : 1, sizeof(long));
+    d.deg = (unsigned char *)calloc(I.N ? I.N : 1, 1);
+    d.st = (char *)calloc(M ? M : 1, 1);
+    d.inK = (char *)calloc(M ? M : 1, 1);
+    for (int a = 0; a < na; a++)
+        for (int j = 0; j < M; j++)
+            if (c->coef[(size_t)a * M + j] > 0) d.posall[a] += c->coef[(size_t)a * M + j];
+    int *cand = (int *)malloc(sizeof(int) * (M ? M : 1));
+    int *ok = (int *)malloc(sizeof(int) * (M ? M : 1));
+    uint64_t rng = seed;
+    int level = 0, attempts = 0;
+    rc = ORC_OK;
+    while (level < depth) {
+        /* the children of the current node, as the canonical tree orders them */
+        int r = -1;
+        for (int i = 0; i < I.N; i++)
+            if (d.deg[i] == 1) { r = i; break; }
+        int nc = 0;
+        if (r >= 0) {
+            for (int k = 0; k < I.npar[r]; k++)
+                if (d.st[I.par[(size_t)r * M + k]] == UNDECIDED) cand[nc++] = I.par[(size_t)r * M + k];
+        } else {
+            for (int f = 0; f < M; f++)
+                if (d.st[f] == UNDECIDED) cand[nc++] = f;
+        }
+        int nok = 0;
+        for (int a = 0; a < nc; a++)
+            if (dfs_add(&d, cand[a])) { dfs_remove(&d, cand[a]); ok[nok++] = a; }
+        if (nok == 0) {  /* dead end: start again from the root */
+            if (++attempts > 10000) { rc = ORC_ERR_INPUT; break; }
+            memset(d.deg, 0, I.N ? I.N : 1);
+            memset(d.st, 0, M ? M : 1);
+            memset(d.inK, 0, M ? M : 1);
+            for (int a = 0; a < na; a++) d.negin[a] = 0;
+            d.size = 0;
+            level = 0;
+            continue;
+        }
+        int a = ok[splitmix64_next(&rng) % (uint64_t)nok];
+        int p = cand[a];
+        if (r >= 0) {
+            for (int b = 0; b < nc; b++)
+                if (b != a) d.st[cand[b]] = OUT;
+        } else {
+            for (int b = 0; b < a; b++) d.st[cand[b]] = OUT;
+        }
+        dfs_add(&d, p);
+        level++;
+    }
+    int W = (M + 63) / 64;
+    for (int w = 0; w < W; w++) { in_mask[w] = 0; out_mask[w] = 0; }
+    for (int j = 0; j < M; j++) {
+        if (d.st[j] == IN) in_mask[j / 64] |= 1ull << (j % 64);
+        if (d.st[j] == OUT) out_mask[j / 64] |= 1ull << (j % 64);
+    }
+    free(cand); free(ok);
+    free(d.posall); free(d.negin); free(d.deg); free(d.st); free(d.inK);
+    incidence_free(&I);
     return rc;
 }
 

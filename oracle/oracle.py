@@ -64,6 +64,11 @@ def lib():
                                              u64p, C.c_uint64, C.POINTER(_Stats)]
             L.orc_enumerate_sweep.argtypes = [C.c_int, C.c_int, C.c_int, u16p, C.POINTER(_Cond),
                                               u64p, C.c_uint64, C.POINTER(_Stats), C.c_int]
+            L.orc_enumerate_dfs_budget.argtypes = [C.c_int, C.c_int, C.c_int, u16p,
+                                                   C.POINTER(_Cond), C.POINTER(_Stats),
+                                                   C.c_uint64]
+            L.orc_walk.argtypes = [C.c_int, C.c_int, C.c_int, u16p, C.POINTER(_Cond), C.c_uint64,
+                                   C.c_int, u64p, u64p]
             L.orc_n2_cycle_sets.argtypes = [C.c_int, u16p, C.c_int]
             L.orc_n2_cycle_sets.restype = C.c_long
             L.orc_n2_cycle_count.argtypes = [C.c_int, u16p]
@@ -201,3 +206,33 @@ def n2_cycle_count(edges: np.ndarray) -> int:
 
 def instance_facets(inst) -> np.ndarray:
     return candidate_facets(inst.kind, inst.n, inst.m, inst.cols)
+
+
+def enumerate_dfs_budget(n, m, facets, max_nodes, cap=CAP_NONE, base_facet=False,
+                         forced_in=None, forced_out=None, affine=None):
+    """O1 in counting mode with a node budget: (count, nodes, probes), or None when the
+    search would exceed max_nodes nodes."""
+    f = np.ascontiguousarray(facets, dtype=np.uint16)
+    cond, keep = _cond(f.size, cap, base_facet, forced_in, forced_out, affine)
+    st = _Stats()
+    rc = lib().orc_enumerate_dfs_budget(n, m, f.size, _p(f, C.c_uint16), C.byref(cond),
+                                        C.byref(st), max_nodes)
+    del keep
+    if rc == -7:
+        return None
+    _check(rc, "enumerate_dfs_budget")
+    return int(st.count), int(st.nodes), int(st.probes)
+
+
+def walk(n, m, facets, seed, depth, cap=CAP_NONE):
+    """Seeded random walk of `depth` steps down the canonical tree; returns the (In, Out)
+    masks of the node reached (uint64 arrays of ceil(M/64) words)."""
+    f = np.ascontiguousarray(facets, dtype=np.uint16)
+    W = max(1, (f.size + 63) // 64)
+    cond, keep = _cond(f.size, cap, False, None, None, None)
+    a = np.zeros(W, dtype=np.uint64)
+    b = np.zeros(W, dtype=np.uint64)
+    _check(lib().orc_walk(n, m, f.size, _p(f, C.c_uint16), C.byref(cond), seed, depth,
+                          _p(a, C.c_uint64), _p(b, C.c_uint64)), "walk")
+    del keep
+    return a, b

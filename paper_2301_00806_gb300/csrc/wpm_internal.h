@@ -24,6 +24,7 @@ enum : uint32_t {
 // Work items: u32 words [inst, flags | floor << 16, size | base << 16, acc], then In[MW],
 // Out[MW], cnt[NW]. Flags (word 1, low 16 bits):
 enum : uint32_t {
+  kItemEmpty = 0u,      // a reserved slot left unused: readers skip it
   kItemFresh = 1u,      // a root: counters not built, not yet counted as a node
   kItemOpen = 2u,       // a counted (and, if a WPM, already emitted) node whose children
                         // have not been counted: the receiver expands it
@@ -117,6 +118,8 @@ struct PassArgs {
 
 // Launchers (wpm_kernels.cu). All return cudaError_t of the launch.
 cudaError_t launch_setup(InstDesc *d_inst, int n_inst, cudaStream_t s);
+// The setup kernel over the instances d_inst[d_ids[0..n_ids)] only.
+cudaError_t launch_setup_ids(InstDesc *d_inst, const int32_t *d_ids, int n_ids, cudaStream_t s);
 cudaError_t launch_roots(const InstDesc *d_inst, int n_ids, const int32_t *d_ids,
                          unsigned long long *ctr, uint32_t *ring, unsigned long long ring_cap,
                          int item_words, int cls_mw, QueueCtl *q, cudaStream_t s);

@@ -109,12 +109,12 @@ __device__ int block_scan(int32_t *arr, int L, int *tmp) {
   return total;
 }
 
-__global__ void __launch_bounds__(256) setup_kernel(InstDesc *insts) {
+__global__ void __launch_bounds__(256) setup_kernel(InstDesc *insts, const int32_t *ids) {
   __shared__ int C[17][17];
   __shared__ int tmp[257];
   __shared__ long long red[256];
   __shared__ uint32_t given[2048];  // kind 2: membership bitmap over all 2^16 vertex masks
-  InstDesc &I = insts[blockIdx.x];
+  InstDesc &I = insts[ids ? ids[blockIdx.x] : (int)blockIdx.x];
   fill_binom(C);
   if (I.kind == 2) {
     for (int i = threadIdx.x; i < 2048; i += blockDim.x) given[i] = 0;
@@ -226,7 +226,13 @@ __global__ void __launch_bounds__(256) setup_kernel(InstDesc *insts) {
 
 cudaError_t launch_setup(InstDesc *d_inst, int n_inst, cudaStream_t s) {
   if (n_inst <= 0) return cudaSuccess;
-  setup_kernel<<<n_inst, 256, 0, s>>>(d_inst);
+  setup_kernel<<<n_inst, 256, 0, s>>>(d_inst, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_setup_ids(InstDesc *d_inst, const int32_t *d_ids, int n_ids, cudaStream_t s) {
+  if (n_ids <= 0) return cudaSuccess;
+  setup_kernel<<<n_ids, 256, 0, s>>>(d_inst, d_ids);
   return cudaGetLastError();
 }
 

@@ -11,6 +11,7 @@
 //   ->  depth-first passes until the work ring is empty  ->  per-instance merge sort
 //   ->  copy-out.
 #include <algorithm>
+#include <chrono>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -23,6 +24,7 @@
 #include <cuda_runtime.h>
 
 #include "wpm.h"
+#include "wpm_host.h"
 #include "wpm_internal.h"
 
 namespace wpm {
@@ -30,7 +32,7 @@ namespace wpm {
 static thread_local std::string t_err;
 static thread_local wpm_run_stats t_stats;
 
-static int fail(int code, const char *fmt, ...) {
+int fail(int code, const char *fmt, ...) {
   char buf[512];
   va_list ap;
   va_start(ap, fmt);
@@ -41,65 +43,6 @@ static int fail(int code, const char *fmt, ...) {
 }
 
 int set_last_error(int code, const char *msg) { return fail(code, "%s", msg); }
-
-#define CUDA_TRY(x)                                                                   \
-  do {                                                                                \
-    cudaError_t e_ = (x);                                                             \
-    if (e_ != cudaSuccess)                                                            \
-      return fail(WPM_ERR_CUDA, "%s failed: %s", #x, cudaGetErrorString(e_));         \
-  } while (0)
-
-#define WPM_TRY(x)                \
-  do {                            \
-    int r_ = (x);                 \
-    if (r_ != WPM_OK) return r_;  \
-  } while (0)
-
-struct DevBuf {
-  void *p = nullptr;
-  size_t cap = 0;
-  int ensure(size_t bytes) {
-    if (bytes <= cap && p) return WPM_OK;
-    release();
-    size_t want = std::max<size_t>(bytes + bytes / 4, 4096);
-    if (cudaMalloc(&p, want) != cudaSuccess) {
-      cudaGetLastError();
-      p = nullptr;
-      return fail(WPM_ERR_NOMEM, "cudaMalloc(%zu bytes) failed", want);
-    }
-    cap = want;
-    return WPM_OK;
-  }
-  void release() {
-    if (p) cudaFree(p);
-    p = nullptr;
-    cap = 0;
-  }
-  template <class T> T *as() const { return reinterpret_cast<T *>(p); }
-};
-
-struct PinBuf {
-  void *p = nullptr;
-  size_t cap = 0;
-  int ensure(size_t bytes) {
-    if (bytes <= cap && p) return WPM_OK;
-    release();
-    size_t want = std::max<size_t>(bytes + bytes / 4, 4096);
-    if (cudaMallocHost(&p, want) != cudaSuccess) {
-      cudaGetLastError();
-      p = nullptr;
-      return fail(WPM_ERR_NOMEM, "cudaMallocHost(%zu bytes) failed", want);
-    }
-    cap = want;
-    return WPM_OK;
-  }
-  void release() {
-    if (p) cudaFreeHost(p);
-    p = nullptr;
-    cap = 0;
-  }
-  template <class T> T *as() const { return reinterpret_cast<T *>(p); }
-};
 
 // Device buffers reused across calls on one device.
 struct Workspace {
@@ -145,17 +88,7 @@ static long long binom(int a, int b) {
   return r;
 }
 
-// An instance as the caller gave it, copied and checked.
-struct HostInst {
-  int kind = 0, n = 0, m = 0;
-  uint32_t cols[kMaxVertices] = {0};
-  std::vector<uint16_t> given;
-  int cap_req = -1, base_req = 0, n_facets_req = -1, n_aff = 0;
-  std::vector<uint64_t> fin, fout;
-  std::vector<int32_t> c0, coef;
-};
-
-static int copy_conditions(const wpm_conditions *c, HostInst &h) {
+int copy_conditions(const wpm_conditions *c, HostInst &h) {
   if (!c) return WPM_OK;
   if (c->ubt_cap < -2) return fail(WPM_ERR_INPUT, "ubt_cap %d is not a cap", c->ubt_cap);
   h.cap_req = c->ubt_cap;
@@ -187,7 +120,7 @@ static int copy_conditions(const wpm_conditions *c, HostInst &h) {
   return WPM_OK;
 }
 
-static int copy_map(const uint32_t *cols, int kind, int n, int m, HostInst &h) {
+int copy_map(const uint32_t *cols, int kind, int n, int m, HostInst &h) {
   if (kind != WPM_LAMBDA_PRIMAL && kind != WPM_LAMBDA_DUAL)
     return fail(WPM_ERR_INPUT, "kind %d is neither primal nor dual", kind);
   if (n < 2 || m <= n || m > WPM_MAX_VERTICES)
@@ -212,7 +145,7 @@ static int copy_map(const uint32_t *cols, int kind, int n, int m, HostInst &h) {
   return WPM_OK;
 }
 
-static int copy_facet_list(const uint16_t *facets, int M, int n, int m, HostInst &h) {
+int copy_facet_list(const uint16_t *facets, int M, int n, int m, HostInst &h) {
   if (n < 2 || m <= n || m > WPM_MAX_VERTICES)
     return fail(WPM_ERR_INPUT, "need 2 <= n < m <= 16 (n=%d, m=%d)", n, m);
   if (M < 0 || M > WPM_MAX_FACETS) return fail(WPM_ERR_LIMIT, "M=%d outside 0..%d", M, WPM_MAX_FACETS);
@@ -246,6 +179,7 @@ struct RunOptions {
   long long ring_items = 0;
   int idle_percent = 0;
   int search = 0;
+  int time_limit_ms = 0;
   bool profile = false;
   bool setup_only = false;  // stop after the setup kernel (candidate facets)
 };
@@ -402,10 +336,16 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
   const long long budget = opt.budget > 0 ? opt.budget : (1ll << 40);
   const long long frontier_target =
       opt.frontier_target > 0 ? opt.frontier_target : 2LL * n_searches;
+  // per-thread searches reserve their slots before returning work, so any ring size is
+  // safe for them; per-warp searches need room for every search's levels at once
+  const unsigned long long room_all = (unsigned long long)n_searches * max_depth;
   unsigned long long ring_cap =
       opt.ring_items > 0 ? (unsigned long long)opt.ring_items
-                         : std::max<unsigned long long>(2ull * n_searches * max_depth,
-                                                        std::max(4ull * n_valid, 1ull << 16));
+                         : std::max<unsigned long long>(
+                               search == kSearchThread ? std::min(2ull * room_all,
+                                                                  64ull * n_searches)
+                                                       : 2ull * room_all,
+                               std::max(4ull * n_valid, 1ull << 16));
   ring_cap = std::max<unsigned long long>(ring_cap, (unsigned long long)n_valid + 1);
   const unsigned long long room = (unsigned long long)n_searches * max_depth;
   const unsigned long long dump_limit = ring_cap > room ? ring_cap - room : 0;
@@ -496,6 +436,14 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
   int pass_no = 0;
 
   // ---- breadth-first expansion, then depth-first passes -----------------------------
+  const auto t_start = std::chrono::steady_clock::now();
+  auto out_of_time = [&]() {
+    if (opt.time_limit_ms <= 0) return false;
+    const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(
+                        std::chrono::steady_clock::now() - t_start).count();
+    return ms >= opt.time_limit_ms;
+  };
+  bool timed_out = false;
   unsigned long long head = 0, tail = hq->tail;
   for (;;) {
     const unsigned long long live = tail - head;
@@ -532,6 +480,10 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
     tail = hq->tail;
   }
   while (tail > head) {
+    if (out_of_time()) {
+      timed_out = true;
+      break;
+    }
     hq->head = head;
     hq->tail = tail;
     hq->limit = tail;
@@ -587,6 +539,10 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
     r.count = c[kCtrCount];
     r.nodes = c[kCtrNodes];
     r.probes = c[kCtrProbes];
+    if (timed_out && c[kCtrLive] != 0) {  // items of this instance are still in the ring
+      r.status = fail(WPM_ERR_TIMEOUT, "instance %d: time limit reached (partial counts)", i);
+      continue;
+    }
     if (list) {
       const unsigned long long fill = c[kCtrFill];
       if (fill != r.count)  // every emission reserves one slot
@@ -705,6 +661,7 @@ static RunOptions options_from(const wpm_tuning *t, int mode) {
     o.idle_percent = t->idle_percent;
     o.search = t->search;
     o.profile = t->profile != 0;
+    o.time_limit_ms = t->time_limit_ms;
   }
   return o;
 }

@@ -301,10 +301,8 @@ struct TSearch {
   }
 
   // Write the node the state holds, restricted to the untried children of entry e (tp0/tp1
-  // hold e's row for a ridge level), as an open item.
-  __device__ void write_item(const PassArgs &a, uint32_t e) {
-    const unsigned long long slot = atomicAdd(&a.q->tail, 1ull);
-    if (slot - a.q->head_start >= a.ring_cap) { atomicOr(&a.q->err, 1ull); return; }
+  // hold e's row for a ridge level), as an open item in the reserved ring slot `slot`.
+  __device__ void write_item(const PassArgs &a, unsigned long long slot, uint32_t e) {
     uint32_t *it = a.ring + (slot % a.ring_cap) * (unsigned long long)K::IW;
     const bool seed = e >> 31;
     it[0] = (uint32_t)inst;
@@ -327,6 +325,12 @@ struct TSearch {
     }
     for (int w = 0; w < nw; w++) it[kItemHeader + 2 * K::MW + w] = cnt(w);
     atomicAdd(&ctr[kCtrN * inst + kCtrLive], 1ull);
+  }
+
+  __device__ void write_empty(const PassArgs &a, unsigned long long slot) {
+    uint32_t *it = a.ring + (slot % a.ring_cap) * (unsigned long long)K::IW;
+    it[0] = 0;
+    it[1] = kItemEmpty;
   }
 
   // Load an item. Returns false when a fresh root fails its checks.
@@ -456,6 +460,7 @@ __global__ void __launch_bounds__(K::TPB) tdfs_kernel(PassArgs a) {
         continue;
       }
       const uint32_t *it = a.ring + (idx % a.ring_cap) * (unsigned long long)K::IW;
+      if ((it[1] & 0xFFFFu) == kItemEmpty) continue;
       S.bind(a.inst, a.outs, a.ctr, (int)it[0]);
       bool fresh;
       if (!S.load(it, fresh)) {
@@ -474,13 +479,29 @@ __global__ void __launch_bounds__(K::TPB) tdfs_kernel(PassArgs a) {
     const bool spent = pass_nodes >= a.budget ||
                        ((pass_nodes & 63) == 63 &&
                         *(volatile unsigned long long *)&a.q->idle >= a.idle_limit);
-    if (spent &&
-        (*(volatile unsigned long long *)&a.q->tail - a.q->head_start) < a.dump_limit) {
+    // return work: reserve one ring slot per open level (a bounded compare-and-swap on the
+    // tail that never passes unconsumed items); without room the search simply goes on
+    unsigned long long base = ~0ull;
+    if (spent) {
+      unsigned long long t = *(volatile unsigned long long *)&a.q->tail;
+      for (int tries = 0; tries < 64; tries++) {
+        if (t + depth - a.q->head_start > a.ring_cap) break;
+        const unsigned long long old = atomicCAS(&a.q->tail, t, t + depth);
+        if (old == t) {
+          base = t;
+          break;
+        }
+        t = old;
+      }
+    }
+    if (base != ~0ull) {
       // every open level's untried children go back to the ring
       if (a.trace) t_dump++;
       uint32_t e = top;
       for (int L = depth; L >= 1; L--) {
-        if (S.has_more(e)) S.write_item(a, e);
+        const unsigned long long slot = base + (depth - L);
+        if (S.has_more(e)) S.write_item(a, slot, e);
+        else S.write_empty(a, slot);
         if (L > 1) {
           e = stk[(L - 2) * stride];
           S.use_entry(e);

@@ -490,6 +490,7 @@ __global__ void __launch_bounds__(256) wexpand_kernel(PassArgs a, int n_items) {
   S.stk = nullptr;
   const unsigned long long idx = a.q->head_start + (unsigned long long)i;
   const uint32_t *it = a.ring + (idx % a.ring_cap) * (unsigned long long)K::IW;
+  if ((it[1] & 0xFFFFu) == kItemEmpty) return;
   S.bind(a.inst, a.outs, a.ctr, (int)it[0]);
   bool fresh;
   if (!S.load(it, fresh)) {
@@ -530,6 +531,7 @@ __global__ void __launch_bounds__(256) wdfs_kernel(PassArgs a) {
       idx = __shfl_sync(kFull, idx, 0);
       if (idx >= a.q->limit) break;  // tickets past the limit are returned by the host
       const uint32_t *it = a.ring + (idx % a.ring_cap) * (unsigned long long)K::IW;
+      if ((it[1] & 0xFFFFu) == kItemEmpty) continue;
       S.bind(a.inst, a.outs, a.ctr, (int)it[0]);
       bool fresh;
       if (!S.load(it, fresh)) {

@@ -68,7 +68,8 @@ class Instance(C.Structure):
 class Tuning(C.Structure):
     _fields_ = [("frontier_target", C.c_int32), ("budget", C.c_int32),
                 ("threads_per_block", C.c_int32), ("idle_percent", C.c_int32),
-                ("ring_items", C.c_int64), ("search", C.c_int32), ("profile", C.c_int32)]
+                ("ring_items", C.c_int64), ("search", C.c_int32), ("profile", C.c_int32),
+                ("time_limit_ms", C.c_int32), ("reserved", C.c_int32)]
 
 
 class RunStats(C.Structure):
@@ -110,9 +111,6 @@ def lib():
             L.wpm_last_error.restype = C.c_char_p
             L.wpm_last_run_stats.argtypes = [C.POINTER(RunStats)]
             L.wpm_release_workspace.argtypes = []
-            if not hasattr(L, "wpm_engine_create"):
-                _lib = L
-                return _lib
             L.wpm_engine_create.argtypes = [C.POINTER(EngineConfig), C.c_void_p, C.POINTER(C.c_void_p)]
             L.wpm_engine_submit.argtypes = [C.c_void_p, C.POINTER(Instance), C.c_int, C.c_uint64,
                                             C.POINTER(C.c_uint64)]
@@ -313,7 +311,7 @@ def enumerate_batch(specs: List[BatchSpec], list_mode=True, capacities=None, tun
     r = lib().wpm_enumerate_batch(insts, n, outs, MODE_LIST if list_mode else MODE_COUNT,
                                   C.byref(tun) if tun is not None else None,
                                   C.c_void_p(st) if st else None)
-    if r not in (OK, ERR_CAPACITY):
+    if r not in (OK, ERR_CAPACITY, ERR_TIMEOUT):
         raise _err(r)
     res = []
     for i in range(n):
@@ -324,6 +322,94 @@ def enumerate_batch(specs: List[BatchSpec], list_mode=True, capacities=None, tun
             masks = bufs[i][: int(o.count) * w].reshape(int(o.count), w).copy()
         res.append(_result(o, masks))
     return res
+
+
+class Engine:
+    """A serving engine (continuous batching, wpm_engine_* of the C ABI).
+
+    submit() queues a job and returns its id; step() admits what fits in device memory and
+    runs one search pass over every resident job; poll() lists finished job ids; result()
+    fetches one (a Result; masks in list mode)."""
+
+    def __init__(self, memory_bytes=0, max_jobs=0, budget=0, max_n=0, stream=None):
+        cfg = EngineConfig()
+        cfg.memory_bytes = memory_bytes
+        cfg.max_jobs = max_jobs
+        cfg.budget = budget
+        cfg.max_n = max_n
+        st = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
+        h = C.c_void_p()
+        r = lib().wpm_engine_create(C.byref(cfg), C.c_void_p(st) if st else None, C.byref(h))
+        if r != OK:
+            raise _err(r)
+        self._h = h
+        self._modes = {}
+
+    def submit(self, kind, n, m, cols, cap=CAP_NONE, base_facet=False, forced_in=None,
+               forced_out=None, affine=None, n_facets=0, list_mode=False, capacity=0) -> int:
+        keep = _Keep()
+        cc = keep.add(np.asarray(cols, dtype=np.uint32))
+        cond = _conditions(cap, base_facet, n_facets, forced_in, forced_out, affine, keep)
+        inst = Instance()
+        inst.kind = _KIND[kind]
+        inst.n = n
+        inst.m = m
+        inst.lambda_cols = _p(cc, C.c_uint32)
+        inst.cond = C.pointer(cond)
+        jid = C.c_uint64()
+        r = lib().wpm_engine_submit(self._h, C.byref(inst), MODE_LIST if list_mode else MODE_COUNT,
+                                    capacity, C.byref(jid))
+        if r != OK:
+            raise _err(r)
+        self._modes[int(jid.value)] = list_mode
+        return int(jid.value)
+
+    def step(self) -> int:
+        n = C.c_int()
+        r = lib().wpm_engine_step(self._h, C.byref(n))
+        if r != OK:
+            raise _err(r)
+        return int(n.value)
+
+    def poll(self, cap: int = 4096) -> List[int]:
+        ids = np.zeros(cap, dtype=np.uint64)
+        k = lib().wpm_engine_poll(self._h, _p(ids, C.c_uint64), cap)
+        if k < 0:
+            raise _err(k)
+        return [int(x) for x in ids[:k]]
+
+    def result(self, job_id: int, capacity: int = 1 << 16) -> Result:
+        list_mode = self._modes.get(job_id, False)
+        while True:
+            o = Output()
+            buf = None
+            if list_mode:
+                buf = np.zeros(max(capacity, 1) * 16, dtype=np.uint64)
+                o.masks = _p(buf, C.c_uint64)
+                o.capacity = capacity
+            r = lib().wpm_engine_result(self._h, job_id, C.byref(o))
+            if r == ERR_CAPACITY and list_mode and o.status == OK and o.count > capacity:
+                capacity = int(o.count)
+                continue
+            self._modes.pop(job_id, None)
+            masks = None
+            if list_mode and o.status == OK:
+                w = int(o.words_per_mask)
+                masks = buf[: int(o.count) * w].reshape(int(o.count), w).copy()
+            res = _result(o, masks)
+            res.status = int(o.status) if r == OK or r == o.status else r
+            return res
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().wpm_engine_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def last_run_stats() -> dict:

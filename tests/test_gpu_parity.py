@@ -359,3 +359,48 @@ def test_n11_orbit_against_oracle(W):
         g = W.enumerate_batch([W.BatchSpec("dual", 11, 15, rows, cap=-2, base_facet=True)],
                               list_mode=False, tuning={"search": search})[0]
         assert (g.count, g.nodes, g.probes) == (c, nd, pr)
+
+
+# ---------------------------------------------------------------------------------------
+# The largest Picard-4 map (n = 11, all 15 nonzero dual rows): 64 seeded subtrees, exact
+# ---------------------------------------------------------------------------------------
+
+def _n11_subtrees():
+    import os
+    from conftest import GOLDEN
+    rows = []
+    for line in open(os.path.join(GOLDEN, "n11_subtrees.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        t = line.split()
+        words = [int(x, 16) for x in t[1:29]]
+        rows.append((int(t[0]), np.array(words[:14], dtype=np.uint64),
+                     np.array(words[14:], dtype=np.uint64), int(t[29]), int(t[30]), int(t[31])))
+    return rows
+
+
+@pytest.mark.parametrize("search", [1, 2], ids=["thread", "warp"])
+def test_n11_subtrees_batched(W, search):
+    inst = I.full_dual_n11(0)
+    rows = _n11_subtrees()
+    assert len(rows) == 64
+    specs = [W.BatchSpec("dual", 11, 15, inst.cols, cap=-2, forced_in=a, forced_out=b, n_facets=840)
+             for _, a, b, _, _, _ in rows]
+    res = W.enumerate_batch(specs, list_mode=False, tuning={"search": search})
+    for r, (seed, _, _, c, nd, pr) in zip(res, rows):
+        assert r.status == 0
+        assert (r.count, r.nodes, r.probes) == (c, nd, pr), seed
+
+
+@pytest.mark.parametrize("search", [1, 2], ids=["thread", "warp"])
+def test_n11_full_map_against_stored_oracle(W, search):
+    """The whole largest Picard-4 map under the cap, against the oracle's stored result
+    (tests/golden/n11_full.txt, written by make_n11_full.py)."""
+    import os
+    from conftest import GOLDEN
+    line = [l for l in open(os.path.join(GOLDEN, "n11_full.txt")) if not l.startswith("#")][0]
+    c, nd, pr = (int(x) for x in line.split())
+    inst = I.full_dual_n11(0)
+    g = W.enumerate_batch([W.BatchSpec("dual", 11, 15, inst.cols, cap=-2)], list_mode=False,
+                          tuning={"search": search})[0]
+    assert (g.count, g.nodes, g.probes) == (c, nd, pr)

@@ -296,3 +296,19 @@ def test_k4_cycle_families_closed_form():
     f = all_nsubsets(2, 4)
     assert O.n2_cycle_sets(f) == 8
     assert O.enumerate_dfs(2, 4, f, list_mode=False)[0] == 8
+
+
+def test_n11_subtree_golden_file_reproduces():
+    """Two lines of tests/golden/n11_subtrees.txt re-derived by the oracle (walk + search)."""
+    import os
+    from conftest import GOLDEN
+    inst = I.full_dual_n11(0)
+    f = O.instance_facets(inst)
+    lines = [l.split() for l in open(os.path.join(GOLDEN, "n11_subtrees.txt")) if not l.startswith("#")]
+    for t in (lines[4], lines[5]):
+        seed = int(t[0])
+        a, b = O.walk(11, 15, f, seed, 6, cap=O.CAP_UBT)
+        assert [f"{int(x):016x}" for x in a] + [f"{int(x):016x}" for x in b] == t[1:29]
+        c, nodes, probes, _ = O.enumerate_dfs(11, 15, f, cap=O.CAP_UBT, forced_in=a, forced_out=b,
+                                              list_mode=False)
+        assert (c, nodes, probes) == (int(t[29]), int(t[30]), int(t[31]))
