@@ -135,8 +135,9 @@ typedef struct {
     int32_t frontier_target;
     int32_t budget;
     int32_t threads_per_block;
-    int32_t idle_percent;   /* a depth-first pass ends (busy searches return their work to
-                               the ring) once this percentage of searches is idle; 0 = 20 */
+    int32_t idle_percent;   /* per-warp searches: a depth-first pass ends (busy searches
+                               return their work to the ring) once this percentage of
+                               searches is idle; 0 = 20                                    */
     int64_t ring_items;
     int32_t search;         /* 1: one search per thread, 2: one search per warp, 0: by size
                                (per thread up to n = 9)                                    */
@@ -145,7 +146,17 @@ typedef struct {
     int32_t time_limit_ms;  /* > 0: launch no depth-first pass after this much wall time;
                                unfinished instances then report WPM_ERR_TIMEOUT with the
                                counts reached so far (no masks)                            */
-    int32_t reserved;
+    /* Per-thread searches hand work over inside a pass: while searches wait for items and
+       the ring holds fewer items than are waiting, a busy search gives its donate_levels
+       shallowest open levels (0 = 4, -1 = none) to the ring and goes on with the rest. A
+       search that leaves a pass with work (budget or time spent, or no room in the ring)
+       gives its feed_levels shallowest levels (0 = 8, -1 = all) while the ring holds fewer
+       than hungry_items items (0 = one per search), and parks the rest until the next
+       pass. donate_every: nodes a search searches between two hand-overs (0 = 2048).     */
+    int32_t feed_levels;
+    int64_t hungry_items;
+    int32_t donate_levels;
+    int32_t donate_every;
 } wpm_tuning;
 
 /* Statistics of the calling thread's last enumeration run. */

@@ -6,12 +6,18 @@
 //      region fits in the engine's output memory (admission by device memory);
 //   2. builds the new jobs' candidate facets and incidence tables (setup kernel over their
 //      slots) and puts their roots in the ring, next to the items of jobs already running;
-//   3. runs one search pass over every item in the ring, whatever job it belongs to;
+//   3. runs one search pass: every search resumes the work it parked at the end of the last
+//      pass or takes items from the ring, whatever job they belong to, until it has spent
+//      its node budget; then it parks what is left (or, while the ring is short of items,
+//      returns it there), so a pass is bounded in time and the ring stays small;
 //   4. retires the jobs none of whose items are left (their per-slot live counter is zero):
 //      sorts their lists on the GPU, copies them to the host and frees slot and memory.
 // A job therefore overlaps on the GPU with whatever else is resident, and its result is the
 // one wpm_enumerate gives (the same kernels, the same canonical tree).
 #include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -80,8 +86,11 @@ struct wpm_engine {
   int max_jobs = 0, max_n = 0;
   long long budget = 4096;
   size_t slot_bytes = 0;
-  unsigned long long ring_cap = 0, dump_limit = 0, idle_limit = 1;
-  DevBuf inst, outd, ctr, tables, cond, ring, stack, aff, q, ids, seg, pool;
+  unsigned long long ring_cap = 0, dump_limit = 0, idle_limit = 1, hungry = 1;
+  unsigned long long parked = 0;  // searches holding parked work after the last pass
+  unsigned long long pass_nodes = 0;
+  DevBuf inst, outd, ctr, tables, cond, ring, ready, stack, aff, q, ids, seg, pool, park;
+  uint32_t epoch = 0;
   PinBuf h_inst, h_outd, h_ctr, h_q, h_ids, h_seg, h_cond;
   size_t pool_bytes = 0;
   std::map<size_t, size_t> free_blocks;  // output pool: offset -> bytes
@@ -263,7 +272,8 @@ int admit(wpm_engine *e) {
 }
 
 int pass(wpm_engine *e) {
-  if (e->tail <= e->head) return WPM_OK;
+  e->pass_nodes = 0;
+  if (e->tail <= e->head && e->parked == 0) return WPM_OK;
   PassArgs pa;
   memset(&pa, 0, sizeof(pa));
   pa.inst = e->inst.as<InstDesc>();
@@ -280,6 +290,13 @@ int pass(wpm_engine *e) {
   pa.budget = e->budget;
   pa.idle_limit = e->idle_limit;
   pa.dump_limit = e->dump_limit;
+  pa.park = e->park.as<uint32_t>();
+  pa.ready = e->ready.as<uint32_t>();
+  pa.epoch = ++e->epoch;
+  pa.hungry = e->hungry;
+  pa.feed = 8;
+  pa.donate = 4;
+  pa.donate_every = 2048;
   QueueCtl *hq = e->h_q.as<QueueCtl>();
   memset(hq, 0, sizeof(QueueCtl));
   hq->head = e->head;
@@ -292,8 +309,11 @@ int pass(wpm_engine *e) {
   CUDA_TRY(cudaStreamSynchronize(e->s));
   if (hq->err & 1ull) return fail(WPM_ERR_NOMEM, "engine work ring overflow");
   if (hq->err & 2ull) return fail(WPM_ERR_LIMIT, "engine search stack overflow");
-  e->head = std::min(hq->head, e->tail);
+  if (hq->err & 4ull) return fail(WPM_ERR_CUDA, "engine: a work item was never published");
+  e->head = std::min(hq->head, hq->tail);  // items written during the pass are taken too
   e->tail = hq->tail;
+  e->parked = hq->parked;
+  e->pass_nodes = hq->nodes;
   return WPM_OK;
 }
 
@@ -382,8 +402,9 @@ int wpm_engine_create(const wpm_engine_config *cfg, void *cuda_stream, wpm_engin
     e->own_stream = true;
   }
   e->k = class_for_n(e->max_n);
-  e->search = e->k <= 5 ? kSearchThread : kSearchWarp;
-  e->tpb = e->search == kSearchThread ? 128 : 256;
+  // per-thread searches, which can park their work between passes
+  e->search = kSearchThread;
+  e->tpb = 128;
   // deepest search: the upper-bound cap of the largest Picard-4 instance (jobs that could go
   // deeper, e.g. uncapped large ones, are refused at admission)
   const int mx = e->max_n;
@@ -405,6 +426,7 @@ int wpm_engine_create(const wpm_engine_config *cfg, void *cuda_stream, wpm_engin
                 (unsigned long long)e->max_jobs;
   e->dump_limit = e->ring_cap > room ? e->ring_cap - room : 0;
   e->idle_limit = std::max<unsigned long long>(1, (unsigned long long)e->n_searches / 5);
+  e->hungry = (unsigned long long)e->n_searches;
   e->pool_bytes = (size_t)mem;
   e->slots.assign(e->max_jobs, nullptr);
   int rc = WPM_OK;
@@ -414,6 +436,7 @@ int wpm_engine_create(const wpm_engine_config *cfg, void *cuda_stream, wpm_engin
       (rc = e->tables.ensure(e->slot_bytes * e->max_jobs)) ||
       (rc = e->cond.ensure(kCondSlotBytes * e->max_jobs)) ||
       (rc = e->ring.ensure(e->ring_cap * e->iw * 4ull)) ||
+      (rc = e->ready.ensure(e->ring_cap * 4ull)) ||
       (rc = e->q.ensure(sizeof(QueueCtl))) || (rc = e->ids.ensure(4ull * e->max_jobs)) ||
       (rc = e->pool.ensure(e->pool_bytes)) ||
       (rc = e->h_inst.ensure(sizeof(InstDesc) * e->max_jobs)) ||
@@ -424,8 +447,13 @@ int wpm_engine_create(const wpm_engine_config *cfg, void *cuda_stream, wpm_engin
     return bail(rc);
   if (e->search == kSearchThread) {
     if ((rc = e->stack.ensure((size_t)n_threads * e->max_depth * 4ull)) ||
-        (rc = e->aff.ensure((size_t)n_threads * 2 * kMaxAffine * 8ull)))
+        (rc = e->aff.ensure((size_t)n_threads * 2 * kMaxAffine * 8ull)) ||
+        (rc = e->park.ensure((size_t)n_threads * (kParkHeader + e->iw) * 4ull)))
       return bail(rc);
+    if (cudaMemsetAsync(e->park.p, 0, e->park.cap, e->s) != cudaSuccess ||
+        cudaMemsetAsync(e->ready.p, 0, e->ready.cap, e->s) != cudaSuccess ||
+        cudaStreamSynchronize(e->s) != cudaSuccess)
+      return bail(fail(WPM_ERR_CUDA, "cudaMemset of the park records failed"));
   }
   e->free_blocks[0] = e->pool.cap;
   *out = e;
@@ -454,9 +482,26 @@ int wpm_engine_submit(wpm_engine *e, const wpm_instance *inst, int mode, uint64_
 
 int wpm_engine_step(wpm_engine *e, int *n_active) {
   if (!e) return fail(WPM_ERR_INPUT, "engine is NULL");
+  static const bool trace = getenv("WPM_TRACE") != nullptr;
+  using clk = std::chrono::steady_clock;
+  const auto t0 = clk::now();
+  const unsigned long long items0 = e->tail - e->head;
   int rc = admit(e);
+  const auto t1 = clk::now();
+  const unsigned long long items1 = e->tail - e->head;
   if (rc == WPM_OK) rc = pass(e);
+  const auto t2 = clk::now();
   if (rc == WPM_OK) rc = retire(e);
+  const auto t3 = clk::now();
+  if (trace) {
+    auto ms = [](clk::duration d) { return std::chrono::duration<double, std::milli>(d).count(); };
+    int a = 0;
+    for (Job *j : e->slots) a += j != nullptr;
+    fprintf(stderr, "[wpm engine] items %llu -> %llu -> %llu; admit %.3f ms, pass %.3f ms, "
+            "retire %.3f ms; active %d, pending %zu; parked %llu, nodes %llu\n", items0, items1,
+            e->tail - e->head, ms(t1 - t0), ms(t2 - t1), ms(t3 - t2), a, e->pending.size(),
+            e->parked, e->pass_nodes);
+  }
   if (n_active) {
     int a = 0;
     for (Job *j : e->slots) a += j != nullptr;
@@ -506,8 +551,8 @@ void wpm_engine_destroy(wpm_engine *e) {
   if (!e) return;
   if (e->s) cudaStreamSynchronize(e->s);
   for (auto &kv : e->jobs) delete kv.second;
-  for (DevBuf *b : {&e->inst, &e->outd, &e->ctr, &e->tables, &e->cond, &e->ring, &e->stack, &e->aff,
-                    &e->q, &e->ids, &e->seg, &e->pool})
+  for (DevBuf *b : {&e->inst, &e->outd, &e->ctr, &e->tables, &e->cond, &e->ring, &e->ready,
+                    &e->stack, &e->aff, &e->q, &e->ids, &e->seg, &e->pool, &e->park})
     b->release();
   for (PinBuf *b : {&e->h_inst, &e->h_outd, &e->h_ctr, &e->h_q, &e->h_ids, &e->h_seg, &e->h_cond})
     b->release();

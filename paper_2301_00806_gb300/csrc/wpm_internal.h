@@ -88,10 +88,13 @@ struct QueueCtl {
   unsigned long long err;         // nonzero: ring overflow (items lost)
   unsigned long long idle;        // searches of this pass that have stopped
   unsigned long long nodes;       // nodes searched in this pass (tracing)
-  unsigned long long pad;
+  unsigned long long parked;      // searches that parked their work at the end of this pass
   // tracing of per-thread passes (PassArgs::trace): warp loop iterations, and the lanes
   // that in them took a search step, fetched an item, returned work, or had stopped
-  unsigned long long iters, lanes_step, lanes_fetch, lanes_dump, lanes_stopped, pad2[3];
+  unsigned long long iters, lanes_step, lanes_fetch, lanes_dump, lanes_stopped;
+  // per-thread passes: searches waiting for an item, searches that have left the pass, and
+  // a flag set when the ring had no room for given work (the pass then ends early)
+  unsigned long long waiting, exited, full;
 };
 
 struct PassArgs {
@@ -114,7 +117,32 @@ struct PassArgs {
   unsigned long long dump_limit;  // a search returns work to the ring only while fewer
                                   // than this many items are in it (so that every search
                                   // dumping max_depth items at once still fits)
+  // Parking (per-thread searches). A pass ends for a search once it has spent its budget or
+  // once idle_limit searches of the pass have run out of items. The search then returns its
+  // shallowest open levels to the ring (`feed` of them while the ring holds fewer than
+  // `hungry` items, else `donate` of them when others are idle, else none) and parks the
+  // rest: it saves its node and stack position in its park record and resumes there in the
+  // next pass. Only the levels given away become ring items, so the ring stays small and a
+  // search never runs on alone for want of room.
+  uint32_t *park;                 // [(kParkHeader + item_words) * n_threads], word w of
+                                  // thread t at [w * n_threads + t]; word 0 of each thread
+                                  // zeroed before the first pass
+  unsigned long long hungry;
+  int donate;
+  int feed;
+  // In-pass hand-over (per-thread searches): an item written during a pass is published by
+  // storing the pass's epoch in ready[slot] after its words; a search that takes a ticket at
+  // or past `limit` waits (bounded) for that before reading it. Epochs only grow over the
+  // life of the buffer, so stale flags never match.
+  uint32_t *ready;                // [ring_cap]
+  uint32_t epoch;
+  int donate_every;               // nodes a search searches between two hand-overs
+  unsigned long long time_left_ns;  // > 0: searches leave the pass (parking their work) this
+                                    // long after it started
 };
+
+// Park record header words (before the item words of the parked node).
+constexpr int kParkHeader = 4;  // valid, top entry, depth | base << 16, unused
 
 // Launchers (wpm_kernels.cu). All return cudaError_t of the launch.
 cudaError_t launch_setup(InstDesc *d_inst, int n_inst, cudaStream_t s);

@@ -50,10 +50,10 @@ struct Workspace {
   int sms = 0;
   cudaStream_t own = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-  DevBuf inst, outd, ctr, arena, cond, ids, q, ring, stack, aff, out, seg, segs, stage;
+  DevBuf inst, outd, ctr, arena, cond, ids, q, ring, ready, stack, aff, park, out, seg, segs, stage;
   PinBuf h_inst, h_outd, h_q, h_ctr, h_cond, h_ids, h_seg, h_segs, h_stage;
   void release() {
-    for (DevBuf *b : {&inst, &outd, &ctr, &arena, &cond, &ids, &q, &ring, &stack, &aff, &out, &seg,
+    for (DevBuf *b : {&inst, &outd, &ctr, &arena, &cond, &ids, &q, &ring, &ready, &stack, &aff, &park, &out, &seg,
                       &segs, &stage})
       b->release();
     for (PinBuf *b : {&h_inst, &h_outd, &h_q, &h_ctr, &h_cond, &h_ids, &h_seg, &h_segs, &h_stage})
@@ -180,6 +180,10 @@ struct RunOptions {
   int idle_percent = 0;
   int search = 0;
   int time_limit_ms = 0;
+  int feed_levels = 0;
+  int donate_levels = 0;
+  int donate_every = 0;
+  long long hungry_items = 0;
   bool profile = false;
   bool setup_only = false;  // stop after the setup kernel (candidate facets)
 };
@@ -363,6 +367,12 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
   if (search == kSearchThread) {
     WPM_TRY(W->stack.ensure((size_t)n_threads * max_depth * 4ull));
     WPM_TRY(W->aff.ensure((size_t)n_threads * 2 * kMaxAffine * 8ull));
+    WPM_TRY(W->park.ensure((size_t)n_threads * (kParkHeader + iw) * 4ull));
+    WPM_TRY(W->ready.ensure(ring_cap * 4ull));
+    // no search is parked yet (word 0 of every park record); no ready flag is raised (the
+    // passes of this run use epochs 1, 2, ...)
+    CUDA_TRY(cudaMemsetAsync(W->park.p, 0, (size_t)n_threads * 4ull, s));
+    CUDA_TRY(cudaMemsetAsync(W->ready.p, 0, ring_cap * 4ull, s));
   }
   const bool list = opt.mode == WPM_MODE_LIST;
   OutDesc *ho = W->h_outd.as<OutDesc>();
@@ -402,6 +412,7 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
   CUDA_TRY(cudaStreamSynchronize(s));
 
   PassArgs pa;
+  memset(&pa, 0, sizeof(pa));  // no parking: every field not set below is zero
   pa.inst = W->inst.as<InstDesc>();
   pa.outs = W->outd.as<OutDesc>();
   pa.ctr = W->ctr.as<unsigned long long>();
@@ -415,6 +426,13 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
   pa.aff_scratch = search == kSearchThread ? W->aff.as<long long>() : nullptr;
   pa.budget = budget;
   pa.dump_limit = dump_limit;
+  pa.park = search == kSearchThread ? W->park.as<uint32_t>() : nullptr;
+  pa.ready = search == kSearchThread ? W->ready.as<uint32_t>() : nullptr;
+  pa.hungry = opt.hungry_items > 0 ? (unsigned long long)opt.hungry_items
+                                    : (unsigned long long)n_searches;
+  pa.feed = opt.feed_levels > 0 ? opt.feed_levels : (opt.feed_levels < 0 ? (1 << 20) : 8);
+  pa.donate = opt.donate_levels > 0 ? opt.donate_levels : (opt.donate_levels < 0 ? 0 : 4);
+  pa.donate_every = opt.donate_every > 0 ? opt.donate_every : 2048;
   const int idle_pct = (opt.idle_percent > 0 && opt.idle_percent <= 100) ? opt.idle_percent : 20;
   pa.idle_limit = std::max<unsigned long long>(1, (unsigned long long)n_searches * idle_pct / 100);
   const bool trace = getenv("WPM_TRACE") != nullptr;
@@ -479,7 +497,8 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
     head = tail;
     tail = hq->tail;
   }
-  while (tail > head) {
+  unsigned long long parked = 0;  // searches that parked work in the last pass
+  while (tail > head || parked > 0) {
     if (out_of_time()) {
       timed_out = true;
       break;
@@ -491,7 +510,16 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
     hq->err = 0;
     hq->idle = 0;
     hq->nodes = 0;
+    hq->parked = 0;
     hq->iters = hq->lanes_step = hq->lanes_fetch = hq->lanes_dump = hq->lanes_stopped = 0;
+    hq->waiting = hq->exited = hq->full = 0;
+    pa.epoch++;
+    if (opt.time_limit_ms > 0) {  // a long pass ends by itself when the time is up
+      const long long used = std::chrono::duration_cast<std::chrono::nanoseconds>(
+                                 std::chrono::steady_clock::now() - t_start).count();
+      pa.time_left_ns = (unsigned long long)std::max<long long>(
+          1, (long long)opt.time_limit_ms * 1000000ll - used);
+    }
     CUDA_TRY(cudaMemcpyAsync(W->q.p, hq, sizeof(QueueCtl), cudaMemcpyHostToDevice, s));
   count_copy(W->q.p, hq, sizeof(QueueCtl), cudaMemcpyHostToDevice);
     if (timed) CUDA_TRY(cudaEventRecord(ev0, s));
@@ -504,16 +532,21 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
     CUDA_TRY(cudaStreamSynchronize(s));
     if (hq->err & 1ull) return fail(WPM_ERR_NOMEM, "work ring overflow (raise ring_items)");
     if (hq->err & 2ull) return fail(WPM_ERR_LIMIT, "search stack overflow");
-    t_stats.items += std::min(hq->head, tail) - head;
+    if (hq->err & 4ull) return fail(WPM_ERR_CUDA, "a work item was never published");
+    // per-thread passes also take items written during the pass (their head never passes
+    // the tail); per-warp passes take only items that were there when it began
+    const unsigned long long taken_to =
+        search == kSearchThread ? std::min(hq->head, hq->tail) : std::min(hq->head, tail);
+    t_stats.items += taken_to - head;
     float ms = 0;
     if (timed) {
       CUDA_TRY(cudaEventElapsedTime(&ms, ev0, ev1));
       t_stats.dfs_ms += ms;
     }
     if (trace) {
-      fprintf(stderr, "[wpm] dfs %d: %llu items, %llu taken, %llu new, %llu nodes, %.3f ms",
-              pass_no++, tail - head, std::min(hq->head, tail) - head, hq->tail - tail, hq->nodes,
-              ms);
+      fprintf(stderr, "[wpm] dfs %d: %llu items, %llu taken, %llu new, %llu parked, %llu nodes, "
+              "%.3f ms", pass_no++, tail - head, taken_to - head, hq->tail - tail, hq->parked,
+              hq->nodes, ms);
       if (hq->iters)
         fprintf(stderr, "; warp iterations %llu, lanes/iteration: step %.2f fetch %.3f stopped "
                 "%.2f; dumps %llu", hq->iters, (double)hq->lanes_step / hq->iters,
@@ -521,8 +554,9 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
                 hq->lanes_dump);
       fprintf(stderr, "\n");
     }
-    head = std::min(hq->head, tail);
+    head = taken_to;
     tail = hq->tail;
+    parked = hq->parked;
   }
 
   // ---- counters ----------------------------------------------------------------------
@@ -662,6 +696,10 @@ static RunOptions options_from(const wpm_tuning *t, int mode) {
     o.search = t->search;
     o.profile = t->profile != 0;
     o.time_limit_ms = t->time_limit_ms;
+    o.feed_levels = t->feed_levels;
+    o.donate_levels = t->donate_levels;
+    o.donate_every = t->donate_every;
+    o.hungry_items = t->hungry_items;
   }
   return o;
 }

@@ -13,6 +13,13 @@
 // returned to the work ring carries only its untried children: a ridge level's tried parents
 // join Out, a seed level's floor moves past its tried facets.
 //
+// A pass ends for a search when it has spent its node budget or when enough searches of the
+// pass have found the ring empty. It then gives its shallowest open levels to the ring (the
+// largest untried subtrees; how many depends on how short of items the ring is) and parks the
+// rest of its work in its own park record (node state, top entry, depth; the stack stays in
+// place), to resume it at the start of the next pass. Giving and parking never change which
+// nodes are searched, so counts do not depend on pass boundaries.
+//
 // Per-thread state lives in shared memory, word w of thread t at [w * TPB + t], so every
 // dynamically indexed access of a warp hits 32 distinct banks:
 //   cnt[NW]  ridge degrees, 2 bits per ridge, 16 ridges per word (values 0, 1, 2)
@@ -325,23 +332,31 @@ struct TSearch {
     }
     for (int w = 0; w < nw; w++) it[kItemHeader + 2 * K::MW + w] = cnt(w);
     atomicAdd(&ctr[kCtrN * inst + kCtrLive], 1ull);
+    publish(a, slot);
   }
 
   __device__ void write_empty(const PassArgs &a, unsigned long long slot) {
     uint32_t *it = a.ring + (slot % a.ring_cap) * (unsigned long long)K::IW;
     it[0] = 0;
     it[1] = kItemEmpty;
+    publish(a, slot);
+  }
+
+  // The item in `slot` is complete: make its words visible, then raise its ready flag.
+  static __device__ __forceinline__ void publish(const PassArgs &a, unsigned long long slot) {
+    __threadfence();
+    *(volatile uint32_t *)&a.ready[slot % a.ring_cap] = a.epoch;
   }
 
   // Load an item. Returns false when a fresh root fails its checks.
   __device__ bool load(const uint32_t *it, bool &fresh) {
-    const uint32_t fl = it[1];
+    const uint32_t fl = __ldcg(it + 1);
     fresh = fl & kItemFresh;
-    floor_ = (fl & kItemSeed) ? (int)(it[2] >> 16) : (int)(fl >> 16);
+    floor_ = (fl & kItemSeed) ? (int)(__ldcg(it + 2) >> 16) : (int)(fl >> 16);
     nodes = probes = count = 0;
     for (int w = 0; w < mw; w++) {
-      inb(w) = it[kItemHeader + w];
-      outb(w) = it[kItemHeader + K::MW + w];
+      inb(w) = __ldcg(it + kItemHeader + w);
+      outb(w) = __ldcg(it + kItemHeader + K::MW + w);
     }
     if (M & 31) outb(mw - 1) |= kFull << (M & 31);
     if (!K::kSummReg) {
@@ -374,8 +389,8 @@ struct TSearch {
       }
       if (cap >= 0 && size > cap) ok = false;
     } else {
-      size = (int)(it[2] & 0xFFFFu);
-      for (int w = 0; w < nw; w++) cnt(w) = it[kItemHeader + 2 * K::MW + w];
+      size = (int)(__ldcg(it + 2) & 0xFFFFu);
+      for (int w = 0; w < nw; w++) cnt(w) = __ldcg(it + kItemHeader + 2 * K::MW + w);
     }
     for (int w = 0; w < nw; w++) set_summ(w, cnt(w));
     for (int e = 0; e < n_aff; e++) {
@@ -397,17 +412,96 @@ struct TSearch {
     return ok;
   }
 
-  __device__ __forceinline__ void flush() {
+  // Counters of the item so far; the item stays live.
+  __device__ __forceinline__ void flush_stats() {
     if (count) atomicAdd(&ctr[kCtrN * inst + kCtrCount], count);
     if (nodes) atomicAdd(&ctr[kCtrN * inst + kCtrNodes], nodes);
     if (probes) atomicAdd(&ctr[kCtrN * inst + kCtrProbes], probes);
-    atomicAdd(&ctr[kCtrN * inst + kCtrLive], (unsigned long long)-1ll);
     nodes = probes = count = 0;
+  }
+
+  // The item is finished: its counters, and one live item less.
+  __device__ __forceinline__ void flush() {
+    flush_stats();
+    atomicAdd(&ctr[kCtrN * inst + kCtrLive], (unsigned long long)-1ll);
+  }
+
+  // Save the whole search (the node it holds and its position: top entry, depth, base) in
+  // the park record `rec` (word w at rec[w * st]); the stack stays where it is.
+  __device__ void park_save(uint32_t *rec, int st, uint32_t top, int depth, int base) {
+    uint32_t *it = rec + (size_t)kParkHeader * st;
+    rec[st] = top;
+    rec[2 * (size_t)st] = (uint32_t)depth | ((uint32_t)base << 16);
+    rec[3 * (size_t)st] = 0;
+    it[0] = (uint32_t)inst;
+    it[(size_t)st] = (uint32_t)floor_;
+    it[2 * (size_t)st] = (uint32_t)size;
+    for (int w = 0; w < mw; w++) it[(size_t)(kItemHeader + w) * st] = inb(w);
+    for (int w = 0; w < mw; w++) it[(size_t)(kItemHeader + K::MW + w) * st] = outb(w);
+    for (int w = 0; w < nw; w++) it[(size_t)(kItemHeader + 2 * K::MW + w) * st] = cnt(w);
+    rec[0] = 1u;
+  }
+
+  // Restore a search saved by park_save (after bind() to the instance in its item word 0).
+  __device__ void park_restore(const uint32_t *rec, int st, uint32_t &top, int &depth,
+                               int &base) {
+    const uint32_t *it = rec + (size_t)kParkHeader * st;
+    top = rec[st];
+    const uint32_t d = rec[2 * (size_t)st];
+    depth = (int)(d & 0xFFFFu);
+    base = (int)(d >> 16);
+    floor_ = (int)it[(size_t)st];
+    size = (int)it[2 * (size_t)st];
+    nodes = probes = count = 0;
+    for (int w = 0; w < mw; w++) inb(w) = it[(size_t)(kItemHeader + w) * st];
+    for (int w = 0; w < mw; w++) outb(w) = it[(size_t)(kItemHeader + K::MW + w) * st];
+    if (!K::kSummReg) {
+      const int sw = (nw + 31) >> 5;
+      for (int s = 0; s < sw; s++) summw(s) = 0;
+    }
+    summ = 0;
+    for (int w = 0; w < nw; w++) {
+      cnt(w) = it[(size_t)(kItemHeader + 2 * K::MW + w) * st];
+      set_summ(w, cnt(w));
+    }
+    for (int e = 0; e < n_aff; e++) {
+      long long si = 0, ni = 0;
+      for (int w = 0; w < mw; w++) {
+        uint32_t x = inb(w);
+        while (x) {
+          const int j = w * 32 + __ffs(x) - 1;
+          x &= x - 1;
+          const long long c = I->aff_coef[e * M + j];
+          si += c;
+          if (c < 0) ni += c;
+        }
+      }
+      aff[e] = si;
+      aff[kMaxAffine + e] = ni;
+    }
+    use_entry(top);
   }
 };
 
+__device__ __forceinline__ unsigned long long vload(const unsigned long long *p) {
+  return *(const volatile unsigned long long *)p;
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Steps of a waiting search before it leaves the pass (a step takes on the order of a
+// microsecond), and polls of a ready flag before the item is reported lost. Both only bound
+// waits that end by themselves in a correct run; a search that leaves early only lowers the
+// parallelism of the rest of the pass.
+constexpr int kMaxIdlePolls = 1 << 14;
+constexpr int kMaxReadyPolls = 1 << 22;
+
 template <class K>
-__global__ void __launch_bounds__(K::TPB) tdfs_kernel(PassArgs a) {
+__global__ void __maxnreg__(96) tdfs_kernel(PassArgs a) {
   extern __shared__ uint32_t smem[];
   TSearch<K> S;
   S.sm = smem + threadIdx.x;
@@ -416,27 +510,43 @@ __global__ void __launch_bounds__(K::TPB) tdfs_kernel(PassArgs a) {
   const int stride = a.n_threads;
   S.aff = a.aff_scratch + (size_t)gtid * 2 * kMaxAffine;
   const int lane = threadIdx.x & 31;
-  int depth = 0;
+  QueueCtl *q = a.q;
+  const unsigned long long t_end = a.time_left_ns ? global_ns() + a.time_left_ns : ~0ull;
+  // Levels 1..depth of the stack are open (entry L at stk[(L - 1) * stride], the top one in
+  // `top`); levels 1..base were given away, so the item is finished when the search pops
+  // back to level base.
+  int depth = 0, base = 0;
   uint32_t top = 0;
-  long long pass_nodes = 0;
-  bool active = true, stop = false;
+  long long pass_nodes = 0, next_check = 63, next_give = 0;
+  // stop: leave the pass this iteration; counted: the leaving search adds itself to
+  // q->exited (a waiting search is already counted in q->waiting)
+  bool active = true, stop = false, counted = false, waiting = false;
+  int polls = 0;
+  uint32_t *rec = a.park + gtid;
+  if (rec[0]) {  // resume the search parked here at the end of the last pass
+    S.bind(a.inst, a.outs, a.ctr, (int)rec[(size_t)kParkHeader * stride]);
+    S.park_restore(rec, stride, top, depth, base);
+    rec[0] = 0;
+  }
   unsigned long long t_iters = 0, t_step = 0, t_fetch = 0, t_dump = 0, t_stopped = 0;
   while (__any_sync(kFull, active)) {
+    // lanes of this warp that hold work (a warp with none backs off while it polls)
+    const unsigned busy = __ballot_sync(kFull, active && !stop && depth > 0);
     if (a.trace) {
       const unsigned act = __ballot_sync(kFull, active && !stop);
-      const unsigned fetch = __ballot_sync(kFull, active && !stop && depth == 0);
       t_iters++;
       t_stopped += 32 - __popc(act);
-      t_fetch += __popc(fetch);
-      t_step += __popc(act & ~fetch);  // includes returning work (counted again below)
+      t_fetch += __popc(act & ~busy);
+      t_step += __popc(busy);  // includes giving work away (counted again below)
     }
     if (stop) {
-      // one update per warp for the threads that stopped this iteration
+      // one update per warp for the searches that leave the pass this iteration
       const unsigned m = __activemask();
       const unsigned done = __reduce_add_sync(m, (unsigned)pass_nodes);
+      const unsigned add = __ballot_sync(m, counted);
       if (lane == __ffs(m) - 1) {
-        atomicAdd(&a.q->idle, (unsigned long long)__popc(m));
-        atomicAdd(&a.q->nodes, (unsigned long long)done);
+        if (add) atomicAdd(&q->exited, (unsigned long long)__popc(add));
+        atomicAdd(&q->nodes, (unsigned long long)done);
       }
       stop = false;
       active = false;
@@ -444,24 +554,91 @@ __global__ void __launch_bounds__(K::TPB) tdfs_kernel(PassArgs a) {
     }
     if (!active) continue;
     if (depth == 0) {
-      if (pass_nodes >= a.budget) {
+      // ---- looking for an item
+      if (pass_nodes >= a.budget || global_ns() >= t_end) {
+        if (waiting) atomicAdd(&q->waiting, (unsigned long long)-1ll);
+        waiting = false;
         stop = true;
+        counted = true;
         continue;
       }
-      // take the next item (warp-aggregated ticket)
+      if (waiting && busy && (++polls & 1)) continue;  // poll every 2nd step beside busy lanes
+      // take tickets for the lanes here (warp-aggregated; never past the tail). Waiting
+      // lanes stop being counted as waiting before the take, so a search that sees every
+      // search waiting or gone and no item left knows that no more items can come.
       const unsigned mask = __activemask();
       const int leader = __ffs(mask) - 1;
-      unsigned long long base = 0;
-      if (lane == leader) base = atomicAdd(&a.q->head, (unsigned long long)__popc(mask));
-      base = __shfl_sync(mask, base, leader);
-      const unsigned long long idx = base + __popc(mask & ((1u << lane) - 1u));
-      if (idx >= a.q->limit) {
-        stop = true;  // tickets past the limit are returned by the host
+      const unsigned n_wait = __popc(__ballot_sync(mask, waiting));
+      unsigned long long h0 = 0, got = 0;
+      if (lane == leader) {
+        // the waiting lanes here leave the count before any take; the lanes left without
+        // an item join it again after
+        const unsigned want = __popc(mask);
+        unsigned long long h = vload(&q->head), t = vload(&q->tail);
+        bool left = false;
+        if (t >= h + (unsigned long long)a.n_threads) {
+          // at least one item per search: even if every other search takes a ticket
+          // meanwhile, these stay below the tail, so a plain add is safe
+          if (n_wait) atomicAdd(&q->waiting, (unsigned long long)-(long long)n_wait);
+          left = true;
+          h = atomicAdd(&q->head, (unsigned long long)want);
+          got = want;
+        } else {
+          // few items: take at most what is there (one compare-and-swap; on a lost race
+          // the lanes try again at their next poll)
+          got = t > h ? t - h : 0;
+          if (got > want) got = want;
+          if (got) {
+            if (n_wait) atomicAdd(&q->waiting, (unsigned long long)-(long long)n_wait);
+            left = true;
+            if (atomicCAS(&q->head, h, h + got) != h) got = 0;
+          }
+        }
+        const unsigned long long join = (want - (unsigned)got) - (left ? 0u : n_wait);
+        if (join) atomicAdd(&q->waiting, join);
+        h0 = h;
+      }
+      h0 = __shfl_sync(mask, h0, leader);
+      got = __shfl_sync(mask, got, leader);
+      const unsigned rank = __popc(mask & ((1u << lane) - 1u));
+      const bool mine = rank < got;
+      if (!mine) {
+        if (!waiting) polls = 0;
+        waiting = true;
+        // every search waits or has left and no item is left: the pass is over
+        const unsigned long long hh = vload(&q->head), tt = vload(&q->tail);
+        if (hh >= tt &&
+            vload(&q->waiting) + vload(&q->exited) >= (unsigned long long)a.n_threads) {
+          stop = true;  // stays counted as waiting
+          counted = false;
+          continue;
+        }
+        if (++polls >= kMaxIdlePolls || (vload(&q->full) && vload(&q->head) >= vload(&q->tail))) {
+          atomicAdd(&q->waiting, (unsigned long long)-1ll);
+          waiting = false;
+          stop = true;
+          counted = true;
+          continue;
+        }
+        if (!busy) __nanosleep(64);
         continue;
       }
+      waiting = false;
+      const unsigned long long idx = h0 + rank;
+      if (idx >= q->limit) {  // written during this pass: wait until it is complete
+        const uint32_t *rf = a.ready + idx % a.ring_cap;
+        int spins = 0;
+        while (*(const volatile uint32_t *)rf != a.epoch && ++spins < kMaxReadyPolls)
+          __nanosleep(32);
+        if (spins >= kMaxReadyPolls) {
+          atomicOr(&q->err, 4ull);
+          continue;
+        }
+        __threadfence();
+      }
       const uint32_t *it = a.ring + (idx % a.ring_cap) * (unsigned long long)K::IW;
-      if ((it[1] & 0xFFFFu) == kItemEmpty) continue;
-      S.bind(a.inst, a.outs, a.ctr, (int)it[0]);
+      if ((__ldcg(it + 1) & 0xFFFFu) == kItemEmpty) continue;
+      S.bind(a.inst, a.outs, a.ctr, (int)__ldcg(it));
       bool fresh;
       if (!S.load(it, fresh)) {
         S.probes++;
@@ -474,44 +651,94 @@ __global__ void __launch_bounds__(K::TPB) tdfs_kernel(PassArgs a) {
       }
       top = S.examine(fresh, S.tp0, S.tp1);
       depth = 1;
+      base = 0;
       continue;
     }
-    const bool spent = pass_nodes >= a.budget ||
-                       ((pass_nodes & 63) == 63 &&
-                        *(volatile unsigned long long *)&a.q->idle >= a.idle_limit);
-    // return work: reserve one ring slot per open level (a bounded compare-and-swap on the
-    // tail that never passes unconsumed items); without room the search simply goes on
-    unsigned long long base = ~0ull;
-    if (spent) {
-      unsigned long long t = *(volatile unsigned long long *)&a.q->tail;
-      for (int tries = 0; tries < 64; tries++) {
-        if (t + depth - a.q->head_start > a.ring_cap) break;
-        const unsigned long long old = atomicCAS(&a.q->tail, t, t + depth);
-        if (old == t) {
-          base = t;
-          break;
-        }
-        t = old;
-      }
-    }
-    if (base != ~0ull) {
-      // every open level's untried children go back to the ring
-      if (a.trace) t_dump++;
-      uint32_t e = top;
-      for (int L = depth; L >= 1; L--) {
-        const unsigned long long slot = base + (depth - L);
-        if (S.has_more(e)) S.write_item(a, slot, e);
-        else S.write_empty(a, slot);
-        if (L > 1) {
-          e = stk[(L - 2) * stride];
-          S.use_entry(e);
-          S.retreat(e);
+    // ---- every 64 nodes: end of the pass (budget, time, full ring), or hand-over
+    if (pass_nodes >= next_check) {
+      next_check = pass_nodes + 64;
+      const bool end = pass_nodes >= a.budget || vload(&q->full) || global_ns() >= t_end;
+      const unsigned long long t = vload(&q->tail), h = vload(&q->head);
+      const unsigned long long items = t > h ? t - h : 0;
+      int give = 0;
+      if (end) {
+        // leaving: give the shallowest levels while the ring is short of items
+        if (items < a.hungry) give = min(a.feed, depth - base);
+      } else {
+        // searches are waiting and the ring cannot serve them all: give the shallowest
+        // levels (the largest untried subtrees), keep the rest; at most once every
+        // donate_every nodes (a hand-over walks the whole stack)
+        if (pass_nodes >= next_give) {
+          const unsigned long long w = vload(&q->waiting);
+          if (w > items) {
+            give = min(a.donate, depth - base - 1);
+            next_give = pass_nodes + a.donate_every;
+          }
         }
       }
-      depth = 0;
-      S.flush();
-      stop = true;
-      continue;
+      // reserve one ring slot per given level (a bounded compare-and-swap on the tail that
+      // never passes items of this pass); without room nothing is given and the pass ends
+      unsigned long long slot0 = ~0ull;
+      if (give > 0) {
+        unsigned long long tt = t;
+        for (int tries = 0; tries < 64; tries++) {
+          if (tt + give - a.q->head_start > a.ring_cap) {
+            atomicExch(&q->full, 1ull);
+            break;
+          }
+          const unsigned long long old = atomicCAS(&q->tail, tt, tt + give);
+          if (old == tt) {
+            slot0 = tt;
+            break;
+          }
+          tt = old;
+        }
+        if (slot0 == ~0ull) give = 0;
+      }
+      if (end || give > 0) {
+        const bool all = end && give == depth - base;
+        // the deepest node is saved before the walk up: for good when leaving, else to
+        // come back to
+        if (!all) S.park_save(rec, stride, top, depth, end ? base + give : base);
+        if (give > 0) {
+          if (a.trace) t_dump++;
+          // walk the state up from the deepest level; levels base+1 .. base+give go to the
+          // ring, deepest first, each with its untried children
+          const int lo = base + 1, hi = base + give;
+          uint32_t e = top;
+          for (int L = depth; L >= lo; L--) {
+            if (L <= hi) {
+              const unsigned long long slot = slot0 + (hi - L);
+              if (S.has_more(e)) S.write_item(a, slot, e);
+              else S.write_empty(a, slot);
+            }
+            if (L > lo) {
+              e = stk[(L - 2) * stride];
+              S.use_entry(e);
+              S.retreat(e);
+            }
+          }
+        }
+        if (end) {
+          if (all) {
+            S.flush();
+          } else {
+            S.flush_stats();
+            atomicAdd(&q->parked, 1ull);
+          }
+          depth = 0;
+          base = 0;
+          stop = true;
+          counted = true;
+          continue;
+        }
+        // back to the deepest node; the given levels are no longer this search's
+        S.flush_stats();
+        int b;
+        S.park_restore(rec, stride, top, depth, b);
+        rec[0] = 0;
+        base = b + give;
+      }
     }
     // One step. Either the top level has a candidate child left (try it: on success add it
     // and push), or the level is done (pop, and remove its parent's child). Both branches
@@ -535,7 +762,9 @@ __global__ void __launch_bounds__(K::TPB) tdfs_kernel(PassArgs a) {
     const bool trying = p >= 0;
     if (!trying) {
       depth--;
-      if (depth == 0) {
+      if (depth == base) {
+        depth = 0;
+        base = 0;
         S.flush();
         continue;
       }

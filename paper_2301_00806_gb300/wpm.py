@@ -69,7 +69,9 @@ class Tuning(C.Structure):
     _fields_ = [("frontier_target", C.c_int32), ("budget", C.c_int32),
                 ("threads_per_block", C.c_int32), ("idle_percent", C.c_int32),
                 ("ring_items", C.c_int64), ("search", C.c_int32), ("profile", C.c_int32),
-                ("time_limit_ms", C.c_int32), ("reserved", C.c_int32)]
+                ("time_limit_ms", C.c_int32), ("feed_levels", C.c_int32),
+                ("hungry_items", C.c_int64), ("donate_levels", C.c_int32),
+                ("donate_every", C.c_int32)]
 
 
 class RunStats(C.Structure):
