@@ -11,6 +11,11 @@ path (candidate facets, ridges, search, per-instance sort) over the 4096 instanc
   e2e    the same metric through the C ABI with host buffers: the step includes copying
          the inputs in and every sorted mask list out to pinned host memory
 
+  serving  the request loop over the serving engine (continuous batching): Poisson
+         arrivals at 200 jobs/s for 60 s, n uniform in {5..9}, each job's full sorted list;
+         p50/p99 latency (completion - arrival) over the jobs finished by the deadline,
+         throughput, and the jobs still queued or running then (N = 1 only)
+
 --impl reference times the CPU oracle (the test oracle, unmodified) on a bounded sample of
 the same workload. Under torchrun each rank runs its own seeded 4096-instance batch (weak
 scaling, no collective on the data path); rank 0 prints the JSON line.
@@ -32,6 +37,11 @@ if ROOT not in sys.path:
 
 METRIC = "search nodes/sec (batched, 4096 Picard-4 instances n=3..8)"
 UNIT = "nodes/s"
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the depth-first kernel per
+# search node, from one ncu capture of a depth-first launch over 256 maps of this mix
+# (501.7 MB for 2,711,713,518 nodes); the roofline's traffic scales it by the step's nodes.
+TDFS_DRAM_BYTES_PER_NODE = 501.7e6 / 2711713518
 
 
 # ------------------------------------------------------------------------------------------
@@ -126,6 +136,28 @@ def algorithmic_ops(res, insts):
     child (node or probe) tests its n ridge counters (load, shift, test: 3 ops each), and each
     accepted child updates its n counters on entry and on exit (load, add, store: 6 ops)."""
     return sum(3 * i.n * (r.nodes + r.probes) + 6 * i.n * r.nodes for r, i in zip(res, insts))
+
+
+def run_serving(args):
+    """The serving measurement: seeded Poisson arrivals served in real time by the engine."""
+    from paper_2301_00806_gb300 import instances as I, serving
+    jobs = I.poisson_jobs(rate=args.serve_rate, duration=args.serve_seconds, n_lo=5, n_hi=9,
+                          seed=args.seed)
+    st = serving.serve(jobs, list_mode=True, max_n=9, deadline_s=args.serve_deadline)
+    sm = st.summary()
+    done_nodes = st.nodes
+    return {
+        "workload": f"Poisson arrivals {args.serve_rate:g}/s for {args.serve_seconds:g} s, "
+                    f"n~U{{5..9}}, m=n+4 dual maps, UBT cap, full sorted lists",
+        "jobs": sm["jobs"], "completed": sm["completed"], "failed": sm["failed"],
+        "unfinished_at_deadline": sm["jobs"] - sm["completed"] - sm["failed"],
+        "deadline_s": args.serve_deadline, "wall_s": sm["wall_s"],
+        "p50_ms": sm["p50_ms"], "p99_ms": sm["p99_ms"], "mean_ms": sm["mean_ms"],
+        "jobs_per_s": sm["jobs_per_s"], "nodes_per_s": sm["nodes_per_s"],
+        "mean_nodes_per_completed_job": done_nodes / max(1, sm["completed"]),
+        "engine_steps": sm["engine_steps"], "max_active_jobs": sm["max_active_jobs"],
+        "latency": "completion minus arrival, over the jobs completed by the deadline",
+    }
 
 
 def run_ours(args, rank, world):
@@ -255,7 +287,10 @@ def run_ours(args, rank, world):
                 "d2h_bytes_per_step": d2h, "ms_per_step": e2e_t * 1000.0},
         "plain_launch": plain,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "int ops/s",
-                     "frac": (achieved / peak_ops) if achieved else None, "traffic": None,
+                     "frac": (achieved / peak_ops) if achieved else None,
+                     "traffic": TDFS_DRAM_BYTES_PER_NODE * nodes_step,
+                     "traffic_per": "step (its depth-first launches), scaled from an ncu "
+                                    "capture on 256 maps of the mix by search nodes",
                      "kernel": "depth-first pass (tdfs_kernel)",
                      "dfs_launches_per_step": dfs_launches / args.steps,
                      "dfs_ms_per_step": dfs_ms / args.steps,
@@ -263,13 +298,15 @@ def run_ours(args, rank, world):
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    if world == 1 and args.serve_seconds > 0:
+        line["serving"] = run_serving(args)
     return line
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--count", type=int, default=4096)
@@ -277,6 +314,11 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--plain-sample", type=int, default=256)
     ap.add_argument("--cpu-stride", type=int, default=64, help="oracle sample: every k-th instance")
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="serving: arrivals per s")
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
+                    help="serving: seconds of arrivals (0 = no serving run)")
+    ap.add_argument("--serve-deadline", type=float, default=90.0,
+                    help="serving: seconds after which the loop stops")
     ap.add_argument("--out-dir", default=os.path.join(ROOT, "bench_out"),
                     help="where the sampled clock log is written")
     args = ap.parse_args()

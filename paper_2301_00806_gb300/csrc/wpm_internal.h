@@ -79,22 +79,27 @@ struct OutDesc {
   unsigned long long pad;
 };
 
-// Work ring control (device).
+// Work ring control (device). The counters that many searches update at once (head, tail,
+// waiting) each have a 128-byte line of their own, away from the fields that searches only
+// read while a pass runs (limit, head_start, full).
 struct QueueCtl {
-  unsigned long long head;        // next item to take (may overshoot limit)
-  unsigned long long tail;        // next free slot
-  unsigned long long limit;       // items of this pass are [head_start, limit)
+  alignas(128) unsigned long long head;  // next item to take (per-warp passes may overshoot
+                                         // limit; per-thread passes never pass the tail)
+  alignas(128) unsigned long long tail;  // next free slot
+  alignas(128) unsigned long long waiting;  // per-thread passes: searches waiting for an item
+  alignas(128) unsigned long long limit;    // items there when the pass began: [head_start, limit)
   unsigned long long head_start;
-  unsigned long long err;         // nonzero: ring overflow (items lost)
-  unsigned long long idle;        // searches of this pass that have stopped
+  unsigned long long full;        // per-thread passes: the ring had no room for given work (the
+                                  // pass then ends early)
+  alignas(128) unsigned long long err;  // nonzero: 1 ring overflow, 2 stack overflow, 4 an
+                                        // item never published
+  unsigned long long idle;        // per-warp passes: searches of this pass that have stopped
   unsigned long long nodes;       // nodes searched in this pass (tracing)
   unsigned long long parked;      // searches that parked their work at the end of this pass
+  unsigned long long exited;      // per-thread passes: searches that have left the pass
   // tracing of per-thread passes (PassArgs::trace): warp loop iterations, and the lanes
   // that in them took a search step, fetched an item, returned work, or had stopped
   unsigned long long iters, lanes_step, lanes_fetch, lanes_dump, lanes_stopped;
-  // per-thread passes: searches waiting for an item, searches that have left the pass, and
-  // a flag set when the ring had no room for given work (the pass then ends early)
-  unsigned long long waiting, exited, full;
 };
 
 struct PassArgs {

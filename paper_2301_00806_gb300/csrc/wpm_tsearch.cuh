@@ -512,6 +512,8 @@ __global__ void __maxnreg__(96) tdfs_kernel(PassArgs a) {
   const int lane = threadIdx.x & 31;
   QueueCtl *q = a.q;
   const unsigned long long t_end = a.time_left_ns ? global_ns() + a.time_left_ns : ~0ull;
+  // items there when the pass began (complete); later ones carry a ready flag
+  const unsigned long long limit = q->limit;
   // Levels 1..depth of the stack are open (entry L at stk[(L - 1) * stride], the top one in
   // `top`); levels 1..base were given away, so the item is finished when the search pops
   // back to level base.
@@ -562,7 +564,7 @@ __global__ void __maxnreg__(96) tdfs_kernel(PassArgs a) {
         counted = true;
         continue;
       }
-      if (waiting && busy && (++polls & 1)) continue;  // poll every 2nd step beside busy lanes
+      if (waiting && busy && (++polls & 3)) continue;  // poll every 4th step beside busy lanes
       // take tickets for the lanes here (warp-aggregated; never past the tail). Waiting
       // lanes stop being counted as waiting before the take, so a search that sees every
       // search waiting or gone and no item left knows that no more items can come.
@@ -625,7 +627,7 @@ __global__ void __maxnreg__(96) tdfs_kernel(PassArgs a) {
       }
       waiting = false;
       const unsigned long long idx = h0 + rank;
-      if (idx >= q->limit) {  // written during this pass: wait until it is complete
+      if (idx >= limit) {  // written during this pass: wait until it is complete
         const uint32_t *rf = a.ready + idx % a.ring_cap;
         int spins = 0;
         while (*(const volatile uint32_t *)rf != a.epoch && ++spins < kMaxReadyPolls)
