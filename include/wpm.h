@@ -157,6 +157,10 @@ typedef struct {
     int64_t hungry_items;
     int32_t donate_levels;
     int32_t donate_every;
+    int32_t graph;          /* 0: the depth-first pass loop runs as one CUDA graph launch (a
+                               conditional while node; not with a time limit or tracing);
+                               -1: the host launches each pass                             */
+    int32_t reserved;
 } wpm_tuning;
 
 /* Statistics of the calling thread's last enumeration run. */
@@ -174,6 +178,8 @@ typedef struct {
     int32_t reserved;
     uint64_t h2d_bytes;        /* bytes copied host -> device by the run                       */
     uint64_t d2h_bytes;        /* bytes copied device -> host by the run                       */
+    uint64_t graph_launches;   /* CUDA graph launches (the depth-first pass loop run on the
+                                  device by a conditional while node)                          */
 } wpm_run_stats;
 
 int wpm_last_run_stats(wpm_run_stats *out);
@@ -213,6 +219,21 @@ int wpm_enumerate_facets(const uint16_t *facets, int M, int n, int m,
  */
 int wpm_enumerate_batch(const wpm_instance *inst, int count, wpm_output *outs, int mode,
                         const wpm_tuning *tuning, void *cuda_stream);
+
+/*
+ * Autotuner of the batched run (the paper has no counterpart). Times a fixed set of
+ * candidate tunings (search mode, i.e. one search per thread or per warp; breadth-first
+ * frontier size; the hand-over chunk of per-thread searches: levels given and nodes between
+ * hand-overs) on a sample of the batch, every k-th instance for about `sample` instances
+ * (0: 256), in counting mode, and writes the fastest to *best. Counts do not depend on the
+ * tuning, so the candidates differ only in time. The choice is also kept, for the rest of
+ * the process, under the batch's signature (the smallest and largest n, and whether any map
+ * is primal): wpm_enumerate_batch with tuning == NULL on a batch of the same signature uses
+ * it. best_ms (optional) receives the winner's time on the sample, in milliseconds.
+ * Errors as wpm_enumerate_batch's; instances that fail their own checks are left out.
+ */
+int wpm_autotune(const wpm_instance *inst, int count, int sample, wpm_tuning *best,
+                 double *best_ms, void *cuda_stream);
 
 /*
  * wpm_candidate_facets with no allocation (the paper has no counterpart: this serves callers

@@ -292,7 +292,7 @@ int pass(wpm_engine *e) {
   pa.dump_limit = e->dump_limit;
   pa.park = e->park.as<uint32_t>();
   pa.ready = e->ready.as<uint32_t>();
-  pa.epoch = ++e->epoch;
+
   pa.hungry = e->hungry;
   pa.feed = 8;
   pa.donate = 4;
@@ -303,6 +303,7 @@ int pass(wpm_engine *e) {
   hq->tail = e->tail;
   hq->limit = e->tail;
   hq->head_start = e->head;
+  hq->epoch = ++e->epoch;
   CUDA_TRY(cudaMemcpyAsync(e->q.p, hq, sizeof(QueueCtl), cudaMemcpyHostToDevice, e->s));
   CUDA_TRY(launch_dfs(e->k, e->search, pa, e->blocks, e->tpb, e->s));
   CUDA_TRY(cudaMemcpyAsync(hq, e->q.p, sizeof(QueueCtl), cudaMemcpyDeviceToHost, e->s));

@@ -91,6 +91,8 @@ struct QueueCtl {
   unsigned long long head_start;
   unsigned long long full;        // per-thread passes: the ring had no room for given work (the
                                   // pass then ends early)
+  unsigned long long epoch;       // per-thread passes: the pass's ready-flag stamp (1, 2, ...)
+  unsigned long long passes;      // depth-first passes run by a graph-driven loop
   alignas(128) unsigned long long err;  // nonzero: 1 ring overflow, 2 stack overflow, 4 an
                                         // item never published
   unsigned long long idle;        // per-warp passes: searches of this pass that have stopped
@@ -136,11 +138,11 @@ struct PassArgs {
   int donate;
   int feed;
   // In-pass hand-over (per-thread searches): an item written during a pass is published by
-  // storing the pass's epoch in ready[slot] after its words; a search that takes a ticket at
-  // or past `limit` waits (bounded) for that before reading it. Epochs only grow over the
-  // life of the buffer, so stale flags never match.
+  // storing the pass's epoch (QueueCtl::epoch) in ready[slot] after its words; a search that
+  // takes a ticket at or past `limit` waits (bounded) for that before reading it. Epochs only
+  // grow over the life of the buffer, so stale flags never match.
   uint32_t *ready;                // [ring_cap]
-  uint32_t epoch;
+  int pad3;
   int donate_every;               // nodes a search searches between two hand-overs
   unsigned long long time_left_ns;  // > 0: searches leave the pass (parking their work) this
                                     // long after it started
@@ -150,6 +152,11 @@ struct PassArgs {
 constexpr int kParkHeader = 4;  // valid, top entry, depth | base << 16, unused
 
 // Launchers (wpm_kernels.cu). All return cudaError_t of the launch.
+// One-thread kernels of a graph-driven pass loop: prep makes the items left by the last pass
+// this pass's and clears the pass counters; check sets the loop's condition h.
+cudaError_t launch_pass_prep(QueueCtl *q, int thread_mode, cudaStream_t s);
+cudaError_t launch_pass_check(QueueCtl *q, int thread_mode, cudaGraphConditionalHandle h,
+                              unsigned long long max_passes, cudaStream_t s);
 cudaError_t launch_setup(InstDesc *d_inst, int n_inst, cudaStream_t s);
 // The setup kernel over the instances d_inst[d_ids[0..n_ids)] only.
 cudaError_t launch_setup_ids(InstDesc *d_inst, const int32_t *d_ids, int n_ids, cudaStream_t s);

@@ -283,6 +283,50 @@ cudaError_t launch_roots(const InstDesc *d_inst, int n_ids, const int32_t *d_ids
 }
 
 // ------------------------------------------------------------------------------------
+// Device-driven pass loop (a CUDA graph with a conditional while node runs prep, the
+// depth-first pass and check until check clears the condition).
+// ------------------------------------------------------------------------------------
+
+// The items left by the last pass become this pass's: [head, tail). Per-warp passes may
+// have overshot head past the old tail (their tickets past it are void).
+__global__ void pass_prep_kernel(QueueCtl *q, int thread_mode) {
+  unsigned long long head = q->head;
+  if (!thread_mode && head > q->limit) head = q->limit;
+  if (head > q->tail) head = q->tail;
+  q->head = head;
+  q->head_start = head;
+  q->limit = q->tail;
+  q->idle = q->nodes = q->parked = q->waiting = q->exited = q->full = 0;
+  q->epoch++;
+  q->passes++;
+}
+
+// Another pass while items are left or searches parked work, no error was raised, and the
+// loop has not run max_passes times (then error 8).
+__global__ void pass_check_kernel(QueueCtl *q, int thread_mode, cudaGraphConditionalHandle h,
+                                  unsigned long long max_passes) {
+  unsigned long long head = q->head;
+  if (!thread_mode && head > q->limit) head = q->limit;
+  bool more = q->err == 0 && (q->tail > head || q->parked > 0);
+  if (more && q->passes >= max_passes) {
+    q->err |= 8ull;
+    more = false;
+  }
+  cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
+cudaError_t launch_pass_prep(QueueCtl *q, int thread_mode, cudaStream_t s) {
+  pass_prep_kernel<<<1, 1, 0, s>>>(q, thread_mode);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pass_check(QueueCtl *q, int thread_mode, cudaGraphConditionalHandle h,
+                              unsigned long long max_passes, cudaStream_t s) {
+  pass_check_kernel<<<1, 1, 0, s>>>(q, thread_mode, h, max_passes);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------
 // Size classes and launchers (the search kernels are instantiated in wpm_class.cu).
 // ------------------------------------------------------------------------------------
 

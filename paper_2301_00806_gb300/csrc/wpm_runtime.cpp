@@ -45,14 +45,36 @@ int fail(int code, const char *fmt, ...) {
 int set_last_error(int code, const char *msg) { return fail(code, "%s", msg); }
 
 // Device buffers reused across calls on one device.
+// The depth-first pass loop as an instantiated CUDA graph: a conditional while node whose
+// body is prep, the pass and check. Kept while the pass's arguments stay the same.
+struct PassGraph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t capture = nullptr;
+  PassArgs pa;
+  int k = -1, search = 0, blocks = 0, tpb = 0;
+  bool unsupported = false;  // conditional nodes are not available: use the host loop
+  void reset() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    exec = nullptr;
+    graph = nullptr;
+    k = -1;
+  }
+};
+
 struct Workspace {
   int device = -1;
   int sms = 0;
   cudaStream_t own = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  PassGraph pg;
   DevBuf inst, outd, ctr, arena, cond, ids, q, ring, ready, stack, aff, park, out, seg, segs, stage;
   PinBuf h_inst, h_outd, h_q, h_ctr, h_cond, h_ids, h_seg, h_segs, h_stage;
   void release() {
+    pg.reset();
+    if (pg.capture) cudaStreamDestroy(pg.capture);
+    pg.capture = nullptr;
     for (DevBuf *b : {&inst, &outd, &ctr, &arena, &cond, &ids, &q, &ring, &ready, &stack, &aff, &park, &out, &seg,
                       &segs, &stage})
       b->release();
@@ -183,6 +205,7 @@ struct RunOptions {
   int feed_levels = 0;
   int donate_levels = 0;
   int donate_every = 0;
+  int graph = 0;  // < 0: host-driven pass loop
   long long hungry_items = 0;
   bool profile = false;
   bool setup_only = false;  // stop after the setup kernel (candidate facets)
@@ -194,6 +217,81 @@ static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 static void count_copy(const void *, const void *, size_t bytes, cudaMemcpyKind kind) {
   if (kind == cudaMemcpyHostToDevice) t_stats.h2d_bytes += bytes;
   else if (kind == cudaMemcpyDeviceToHost) t_stats.d2h_bytes += bytes;
+}
+
+// Most passes a graph-driven loop runs before it stops with error 8.
+constexpr unsigned long long kMaxGraphPasses = 1ull << 20;
+
+// Launch the depth-first pass loop as a CUDA graph on `s` (building it first unless the last
+// one has the same arguments). Returns cudaErrorNotSupported when conditional graph nodes
+// are not available (the caller then runs the host loop).
+static cudaError_t launch_pass_graph(Workspace *W, const PassArgs &pa, int k, int search,
+                                     int blocks, int tpb, cudaStream_t s) {
+  PassGraph &G = W->pg;
+  if (G.unsupported) return cudaErrorNotSupported;
+  const bool same = G.exec && G.k == k && G.search == search && G.blocks == blocks &&
+                    G.tpb == tpb && memcmp(&G.pa, &pa, sizeof(PassArgs)) == 0;
+  if (!same) {
+    G.reset();
+    if (!G.capture) {
+      cudaError_t e = cudaStreamCreateWithFlags(&G.capture, cudaStreamNonBlocking);
+      if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = cudaGraphCreate(&G.graph, 0);
+    if (e != cudaSuccess) return e;
+    cudaGraphConditionalHandle h;
+    if (cudaGraphConditionalHandleCreate(&h, G.graph, 1, cudaGraphCondAssignDefault) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      G.reset();
+      G.unsupported = true;
+      return cudaErrorNotSupported;
+    }
+    // (the parameter union has no default constructor in C++: zeroed storage instead)
+    alignas(cudaGraphNodeParams) unsigned char cp_bytes[sizeof(cudaGraphNodeParams)];
+    memset(cp_bytes, 0, sizeof(cp_bytes));
+    cudaGraphNodeParams &cp = *reinterpret_cast<cudaGraphNodeParams *>(cp_bytes);
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, G.graph, nullptr, nullptr, 0, &cp);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      G.reset();
+      G.unsupported = true;
+      return cudaErrorNotSupported;
+    }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    const int thread_mode = search == kSearchThread;
+    e = cudaStreamBeginCaptureToGraph(G.capture, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) {
+      G.reset();
+      return e;
+    }
+    cudaError_t e1 = launch_pass_prep(pa.q, thread_mode, G.capture);
+    cudaError_t e2 = launch_dfs(k, search, pa, blocks, tpb, G.capture);
+    cudaError_t e3 = launch_pass_check(pa.q, thread_mode, h, kMaxGraphPasses, G.capture);
+    cudaGraph_t captured = nullptr;
+    e = cudaStreamEndCapture(G.capture, &captured);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || e != cudaSuccess) {
+      G.reset();
+      return e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : (e3 != cudaSuccess ? e3 : e));
+    }
+    e = cudaGraphInstantiate(&G.exec, G.graph, 0);
+    if (e != cudaSuccess) {
+      G.reset();
+      return e;
+    }
+    G.pa = pa;
+    G.k = k;
+    G.search = search;
+    G.blocks = blocks;
+    G.tpb = tpb;
+  }
+  return cudaGraphLaunch(G.exec, s);
 }
 
 // The engine of every entry point: run the instances `hi` on stream `s`.
@@ -499,6 +597,42 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
     tail = hq->tail;
   }
   unsigned long long parked = 0;  // searches that parked work in the last pass
+  unsigned long long epoch = 0;   // ready-flag stamp of the last pass (the flags were zeroed)
+  // Without tracing or a time limit the pass loop runs on the device: one graph launch, whose
+  // conditional while node repeats prep, pass and check until no item or parked search is
+  // left (no host round trip between passes).
+  if (tail > head && !trace && opt.time_limit_ms <= 0 && opt.graph >= 0) {
+    memset(hq, 0, sizeof(QueueCtl));
+    hq->head = head;
+    hq->tail = tail;
+    hq->limit = tail;
+    hq->head_start = head;
+    CUDA_TRY(cudaMemcpyAsync(W->q.p, hq, sizeof(QueueCtl), cudaMemcpyHostToDevice, s));
+    count_copy(W->q.p, hq, sizeof(QueueCtl), cudaMemcpyHostToDevice);
+    if (timed) CUDA_TRY(cudaEventRecord(ev0, s));
+    const cudaError_t ge = launch_pass_graph(W, pa, k, search, blocks, tpb, s);
+    if (ge == cudaSuccess) {
+      if (timed) CUDA_TRY(cudaEventRecord(ev1, s));
+      CUDA_TRY(cudaMemcpyAsync(hq, W->q.p, sizeof(QueueCtl), cudaMemcpyDeviceToHost, s));
+      count_copy(hq, W->q.p, sizeof(QueueCtl), cudaMemcpyDeviceToHost);
+      CUDA_TRY(cudaStreamSynchronize(s));
+      if (hq->err & 1ull) return fail(WPM_ERR_NOMEM, "work ring overflow (raise ring_items)");
+      if (hq->err & 2ull) return fail(WPM_ERR_LIMIT, "search stack overflow");
+      if (hq->err & 4ull) return fail(WPM_ERR_CUDA, "a work item was never published");
+      if (hq->err & 8ull) return fail(WPM_ERR_CUDA, "pass loop did not finish");
+      t_stats.dfs_passes += hq->passes;
+      t_stats.kernel_launches += 3 * hq->passes;
+      t_stats.graph_launches++;
+      if (timed) {
+        float ms = 0;
+        CUDA_TRY(cudaEventElapsedTime(&ms, ev0, ev1));
+        t_stats.dfs_ms += ms;
+      }
+      head = tail = 0;  // all done
+    } else if (ge != cudaErrorNotSupported) {
+      return fail(WPM_ERR_CUDA, "pass graph: %s", cudaGetErrorString(ge));
+    }
+  }
   while (tail > head || parked > 0) {
     if (out_of_time()) {
       timed_out = true;
@@ -514,7 +648,7 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
     hq->parked = 0;
     hq->iters = hq->lanes_step = hq->lanes_fetch = hq->lanes_dump = hq->lanes_stopped = 0;
     hq->waiting = hq->exited = hq->full = 0;
-    pa.epoch++;
+    hq->epoch = ++epoch;
     if (opt.time_limit_ms > 0) {  // a long pass ends by itself when the time is up
       const long long used = std::chrono::duration_cast<std::chrono::nanoseconds>(
                                  std::chrono::steady_clock::now() - t_start).count();
@@ -700,6 +834,7 @@ static RunOptions options_from(const wpm_tuning *t, int mode) {
     o.feed_levels = t->feed_levels;
     o.donate_levels = t->donate_levels;
     o.donate_every = t->donate_every;
+    o.graph = t->graph;
     o.hungry_items = t->hungry_items;
   }
   return o;
@@ -728,6 +863,50 @@ static int single(HostInst &h, wpm_output *out, int mode) {
 }  // namespace wpm
 
 using namespace wpm;
+
+// ---- autotuner ---------------------------------------------------------------------------
+// Signature of a batch: smallest and largest n, and whether any map is primal.
+static uint64_t batch_signature(const wpm_instance *inst, int count) {
+  int lo = 99, hi = 0, primal = 0;
+  for (int i = 0; i < count; i++) {
+    lo = std::min(lo, (int)inst[i].n);
+    hi = std::max(hi, (int)inst[i].n);
+    primal |= inst[i].kind == WPM_LAMBDA_PRIMAL;
+  }
+  return ((uint64_t)lo << 16) | ((uint64_t)hi << 1) | (uint64_t)primal;
+}
+
+static std::map<uint64_t, wpm_tuning> g_tuned;  // guarded by g_mu
+
+static bool tuned_for(const wpm_instance *inst, int count, wpm_tuning *out) {
+  if (count <= 0 || !inst) return false;
+  auto it = g_tuned.find(batch_signature(inst, count));
+  if (it == g_tuned.end()) return false;
+  *out = it->second;
+  return true;
+}
+
+// The candidates: per-warp searches (two frontier sizes), per-thread searches with three
+// hand-over chunks and a larger frontier.
+static std::vector<wpm_tuning> tune_candidates() {
+  std::vector<wpm_tuning> c;
+  auto add = [&](int search, int frontier, int donate, int every) {
+    wpm_tuning t;
+    memset(&t, 0, sizeof(t));
+    t.search = search;
+    t.frontier_target = frontier;
+    t.donate_levels = donate;
+    t.donate_every = every;
+    c.push_back(t);
+  };
+  add(kSearchWarp, 0, 0, 0);
+  add(kSearchWarp, 1 << 18, 0, 0);
+  add(kSearchThread, 0, 4, 2048);
+  add(kSearchThread, 0, 2, 512);
+  add(kSearchThread, 0, 8, 8192);
+  add(kSearchThread, 1 << 19, 4, 2048);
+  return c;
+}
 
 extern "C" {
 
@@ -804,6 +983,8 @@ int wpm_enumerate_batch(const wpm_instance *inst, int count, wpm_output *outs, i
   std::lock_guard<std::mutex> g(g_mu);
   t_err.clear();
   if (count < 0 || (count > 0 && (!inst || !outs))) return fail(WPM_ERR_INPUT, "bad batch arrays");
+  wpm_tuning tuned;
+  if (!tuning && tuned_for(inst, count, &tuned)) tuning = &tuned;
   std::vector<HostInst> hi;
   std::vector<int> where;  // hi index -> caller index
   std::vector<int> status(count, WPM_OK);
@@ -836,6 +1017,48 @@ int wpm_enumerate_batch(const wpm_instance *inst, int count, wpm_output *outs, i
     if (status[i] != WPM_OK && first == WPM_OK) first = status[i];
   }
   return first;
+}
+
+int wpm_autotune(const wpm_instance *inst, int count, int sample, wpm_tuning *best,
+                 double *best_ms, void *cuda_stream) {
+  std::lock_guard<std::mutex> g(g_mu);
+  t_err.clear();
+  if (count <= 0 || !inst || !best) return fail(WPM_ERR_INPUT, "bad autotune arguments");
+  if (sample <= 0) sample = 256;
+  const int stride = std::max(1, count / sample);
+  std::vector<HostInst> hi;
+  for (int i = 0; i < count; i += stride) {
+    HostInst h;
+    if (copy_map(inst[i].lambda_cols, inst[i].kind, inst[i].n, inst[i].m, h) != WPM_OK ||
+        copy_conditions(inst[i].cond, h) != WPM_OK)
+      continue;
+    hi.push_back(std::move(h));
+  }
+  if (hi.empty()) return fail(WPM_ERR_INPUT, "autotune: no valid instance in the sample");
+  Workspace *W = nullptr;
+  WPM_TRY(get_workspace(&W));
+  cudaStream_t s = cuda_stream ? (cudaStream_t)cuda_stream : W->own;
+  double best_t = 1e300;
+  wpm_tuning win;
+  memset(&win, 0, sizeof(win));
+  std::vector<InstResult> res;
+  for (const wpm_tuning &c : tune_candidates()) {
+    std::vector<HostInst> h2 = hi;
+    CUDA_TRY(cudaStreamSynchronize(s));
+    const auto t0 = std::chrono::steady_clock::now();
+    WPM_TRY(run(W, h2, options_from(&c, WPM_MODE_COUNT), s, nullptr, res, nullptr));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    const double ms = std::chrono::duration<double, std::milli>(
+                          std::chrono::steady_clock::now() - t0).count();
+    if (ms < best_t) {
+      best_t = ms;
+      win = c;
+    }
+  }
+  g_tuned[batch_signature(inst, count)] = win;
+  *best = win;
+  if (best_ms) *best_ms = best_t;
+  return WPM_OK;
 }
 
 }  // extern "C"

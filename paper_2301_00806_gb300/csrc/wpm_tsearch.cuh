@@ -84,6 +84,7 @@ struct TSearch {
   uint4 tp0, tp1;  // parents row of the top entry (ridge levels)
   // statistics of the current item
   unsigned long long nodes, probes, count;
+  uint32_t epoch;  // the pass's ready-flag stamp
 
   __device__ __forceinline__ uint32_t &cnt(int w) { return sm[w * K::TPB]; }
   __device__ __forceinline__ uint32_t &inb(int w) { return sm[(K::NW + w) * K::TPB]; }
@@ -343,9 +344,9 @@ struct TSearch {
   }
 
   // The item in `slot` is complete: make its words visible, then raise its ready flag.
-  static __device__ __forceinline__ void publish(const PassArgs &a, unsigned long long slot) {
+  __device__ __forceinline__ void publish(const PassArgs &a, unsigned long long slot) {
     __threadfence();
-    *(volatile uint32_t *)&a.ready[slot % a.ring_cap] = a.epoch;
+    *(volatile uint32_t *)&a.ready[slot % a.ring_cap] = epoch;
   }
 
   // Load an item. Returns false when a fresh root fails its checks.
@@ -514,6 +515,7 @@ __global__ void __maxnreg__(96) tdfs_kernel(PassArgs a) {
   const unsigned long long t_end = a.time_left_ns ? global_ns() + a.time_left_ns : ~0ull;
   // items there when the pass began (complete); later ones carry a ready flag
   const unsigned long long limit = q->limit;
+  S.epoch = (uint32_t)q->epoch;
   // Levels 1..depth of the stack are open (entry L at stk[(L - 1) * stride], the top one in
   // `top`); levels 1..base were given away, so the item is finished when the search pops
   // back to level base.
@@ -630,7 +632,7 @@ __global__ void __maxnreg__(96) tdfs_kernel(PassArgs a) {
       if (idx >= limit) {  // written during this pass: wait until it is complete
         const uint32_t *rf = a.ready + idx % a.ring_cap;
         int spins = 0;
-        while (*(const volatile uint32_t *)rf != a.epoch && ++spins < kMaxReadyPolls)
+        while (*(const volatile uint32_t *)rf != S.epoch && ++spins < kMaxReadyPolls)
           __nanosleep(32);
         if (spins >= kMaxReadyPolls) {
           atomicOr(&q->err, 4ull);

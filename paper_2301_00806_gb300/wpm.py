@@ -71,7 +71,7 @@ class Tuning(C.Structure):
                 ("ring_items", C.c_int64), ("search", C.c_int32), ("profile", C.c_int32),
                 ("time_limit_ms", C.c_int32), ("feed_levels", C.c_int32),
                 ("hungry_items", C.c_int64), ("donate_levels", C.c_int32),
-                ("donate_every", C.c_int32)]
+                ("donate_every", C.c_int32), ("graph", C.c_int32), ("reserved", C.c_int32)]
 
 
 class RunStats(C.Structure):
@@ -79,7 +79,8 @@ class RunStats(C.Structure):
                 ("dfs_passes", C.c_uint64), ("sort_passes", C.c_uint64), ("items", C.c_uint64),
                 ("dfs_ms", C.c_double), ("expand_ms", C.c_double), ("search", C.c_int32),
                 ("size_class", C.c_int32), ("searches", C.c_int32), ("reserved", C.c_int32),
-                ("h2d_bytes", C.c_uint64), ("d2h_bytes", C.c_uint64)]
+                ("h2d_bytes", C.c_uint64), ("d2h_bytes", C.c_uint64),
+                ("graph_launches", C.c_uint64)]
 
 
 class EngineConfig(C.Structure):
@@ -111,6 +112,8 @@ def lib():
             L.wpm_enumerate_batch.argtypes = [C.POINTER(Instance), C.c_int, C.POINTER(Output),
                                               C.c_int, C.POINTER(Tuning), C.c_void_p]
             L.wpm_last_error.restype = C.c_char_p
+            L.wpm_autotune.argtypes = [C.POINTER(Instance), C.c_int, C.c_int, C.POINTER(Tuning),
+                                       C.POINTER(C.c_double), C.c_void_p]
             L.wpm_last_run_stats.argtypes = [C.POINTER(RunStats)]
             L.wpm_release_workspace.argtypes = []
             L.wpm_engine_create.argtypes = [C.POINTER(EngineConfig), C.c_void_p, C.POINTER(C.c_void_p)]
@@ -412,6 +415,34 @@ class Engine:
             self.close()
         except Exception:
             pass
+
+
+def autotune(specs: List[BatchSpec], sample: int = 0, stream=None):
+    """wpm_autotune: time the library's candidate tunings on a sample of the batch and keep
+    the fastest for batches of the same signature. Returns (tuning dict, ms on the sample)."""
+    n = len(specs)
+    keep = _Keep()
+    insts = (Instance * max(n, 1))()
+    for i in range(n):
+        s = specs[i]
+        cc = keep.add(np.asarray(s.cols, dtype=np.uint32))
+        cond = _conditions(s.cap, s.base_facet, s.n_facets, s.forced_in, s.forced_out, s.affine,
+                           keep)
+        keep.add(cond)
+        insts[i].kind = _KIND[s.kind]
+        insts[i].n = s.n
+        insts[i].m = s.m
+        insts[i].lambda_cols = _p(cc, C.c_uint32)
+        insts[i].cond = C.pointer(cond)
+    st = None
+    if stream is not None:
+        st = stream if isinstance(stream, int) else stream.cuda_stream
+    best = Tuning()
+    ms = C.c_double()
+    r = lib().wpm_autotune(insts, n, sample, C.byref(best), C.byref(ms), st)
+    if r != OK:
+        raise _err(r)
+    return {f: getattr(best, f) for f, _ in Tuning._fields_ if f != "reserved"}, ms.value
 
 
 def last_run_stats() -> dict:

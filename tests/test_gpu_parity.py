@@ -142,9 +142,21 @@ def _mixed(count=48, seed=11):
                                     {"search": 1, "budget": 2, "frontier_target": 1},
                                     {"search": 2},
                                     {"search": 2, "budget": 1, "frontier_target": 1},
-                                    {"search": 2, "budget": 5, "idle_percent": 100, "threads_per_block": 64}],
+                                    {"search": 2, "budget": 5, "idle_percent": 100, "threads_per_block": 64},
+                                    {"search": 1},
+                                    {"search": 1, "budget": 1},
+                                    {"search": 1, "donate_levels": -1},
+                                    {"search": 1, "donate_levels": 16, "donate_every": 1},
+                                    {"search": 1, "feed_levels": -1, "hungry_items": 1 << 40, "budget": 9},
+                                    {"search": 1, "feed_levels": 1, "hungry_items": 1, "budget": 5},
+                                    {"search": 1, "ring_items": 3000, "donate_every": 1, "frontier_target": 1},
+                                    {"search": 1, "graph": -1, "donate_every": 1},
+                                    {"search": 2, "graph": -1}],
                          ids=["default", "budget1", "nofrontier", "wide", "smallring", "nobudget",
-                              "thread_budget2", "warp", "warp_budget1", "warp_small"])
+                              "thread_budget2", "warp", "warp_budget1", "warp_small", "thread",
+                              "thread_budget1", "thread_nodonate", "thread_donate_often",
+                              "thread_feed_all", "thread_feed_one", "thread_ring_full",
+                              "thread_host_loop", "warp_host_loop"])
 def test_mixed_batch_with_tunings(W, tuning):
     insts = _mixed()
     orc = [oracle_run(inst, cap=-2)[1] for inst in insts]
@@ -153,6 +165,41 @@ def test_mixed_batch_with_tunings(W, tuning):
     for g, o in zip(res, orc):
         assert g.status == 0
         assert_same(g, o)
+
+
+@pytest.mark.parametrize("search", [1, 2])
+def test_pass_loop_graph_matches_host_loop(W, search):
+    """The depth-first pass loop run as one CUDA graph launch (a conditional while node) gives
+    what the host-driven loop gives, counters included."""
+    insts = _mixed(24, seed=5)
+    specs = [W.BatchSpec("dual", i.n, i.m, i.cols, cap=-2) for i in insts]
+    g = W.enumerate_batch(specs, list_mode=True, capacities=[8192] * len(specs),
+                          tuning={"search": search})
+    sg = W.last_run_stats()
+    h = W.enumerate_batch(specs, list_mode=True, capacities=[8192] * len(specs),
+                          tuning={"search": search, "graph": -1})
+    sh = W.last_run_stats()
+    assert sg["graph_launches"] == 1 and sh["graph_launches"] == 0
+    assert sg["dfs_passes"] >= 1
+    for a, b in zip(g, h):
+        assert (a.status, a.count, a.nodes, a.probes) == (b.status, b.count, b.nodes, b.probes)
+        assert np.array_equal(a.masks, b.masks)
+
+
+def test_autotune_choice_is_used_and_exact(W):
+    """wpm_autotune returns one of its candidates; a batch of the same signature run with
+    tuning NULL then uses it, and every tuning gives the oracle's results."""
+    insts = _mixed(32, seed=9)
+    specs = [W.BatchSpec("dual", i.n, i.m, i.cols, cap=-2) for i in insts]
+    best, ms = W.autotune(specs, sample=16)
+    assert best["search"] in (1, 2) and ms > 0
+    orc = [oracle_run(inst, cap=-2)[1] for inst in insts]
+    for tun in (None, {k: v for k, v in best.items() if v}):
+        res = W.enumerate_batch(specs, list_mode=True, capacities=[o[0] + 1 for o in orc],
+                                tuning=tun)
+        for r, o in zip(res, orc):
+            assert_same(r, o)
+        assert W.last_run_stats()["search"] == best["search"]
 
 
 def test_batch_into_device_tensors(W):
