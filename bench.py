@@ -11,6 +11,9 @@ path (candidate facets, ridges, search, per-instance sort) over the 4096 instanc
   e2e    the same metric through the C ABI with host buffers: the step includes copying
          the inputs in and every sorted mask list out to pinned host memory
 
+  paper_table1  every IDCM orbit of n = 8..11 under the cap alone (the paper's Table 1
+         workload), seconds per orbit beside the paper's times (other hardware, other
+         algorithm: context only)
   serving  the request loop over the serving engine (continuous batching): Poisson
          arrivals at 200 jobs/s for 60 s, n uniform in {5..9}, each job's full sorted list;
          p50/p99 latency (completion - arrival) over the jobs finished by the deadline,
@@ -160,6 +163,39 @@ def run_serving(args):
     }
 
 
+# Table 1 of the paper: time per IDCM orbit of its kernel sweep under the upper-bound cap,
+# on an Nvidia Quadro A5000 (n = 11: the authors' estimate, not a run).
+PAPER_TABLE1_SECONDS_PER_ORBIT = {8: 15 * 60.0, 9: 2 * 3600.0, 10: 12 * 86400.0,
+                                  11: 3 * 365 * 86400.0}
+
+
+def run_paper_table1(stream):
+    """Every IDCM orbit of n = 8..11 (one map each, the cap only, counting mode) as one
+    batched run per n: seconds per orbit beside the paper's."""
+    import torch
+    from paper_2301_00806_gb300 import instances as I, wpm
+    rows = []
+    for n in sorted(PAPER_TABLE1_SECONDS_PER_ORBIT):
+        reps = I.idcm_orbit_reps(n)
+        specs = [wpm.BatchSpec("dual", n, n + 4, r, cap=wpm.CAP_UBT) for r in reps]
+        wpm.enumerate_batch(specs[:1], list_mode=False, stream=stream)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = wpm.enumerate_batch(specs, list_mode=False, stream=stream)
+        dt = time.perf_counter() - t0
+        assert all(r.status == 0 for r in res)
+        per = dt / len(reps)
+        paper = PAPER_TABLE1_SECONDS_PER_ORBIT[n]
+        rows.append({"n": n, "orbits": len(reps), "wpms": sum(r.count for r in res),
+                     "nodes": sum(r.nodes for r in res), "seconds_per_orbit": per,
+                     "paper_seconds_per_orbit": paper, "paper_over_ours": paper / per})
+    return {"workload": "one map per IDCM orbit (Section 4.2), UBT cap only, counting mode, "
+                        "each n one batched call timed end to end on the host",
+            "paper_hardware": "Nvidia Quadro A5000, kernel-combination sweep (Algorithm 2.2); "
+                              "n = 11 is the paper's estimate",
+            "rows": rows}
+
+
 def run_ours(args, rank, world):
     import numpy as np
     import torch
@@ -304,6 +340,8 @@ def run_ours(args, rank, world):
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    if world == 1 and args.table1:
+        line["paper_table1"] = run_paper_table1(stream)
     if world == 1 and args.serve_seconds > 0:
         line["serving"] = run_serving(args)
     return line
@@ -320,6 +358,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--plain-sample", type=int, default=256)
     ap.add_argument("--cpu-stride", type=int, default=64, help="oracle sample: every k-th instance")
+    ap.add_argument("--table1", type=int, default=1,
+                    help="time every IDCM orbit of n = 8..11 beside the paper's Table 1")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="serving: arrivals per s")
     ap.add_argument("--serve-seconds", type=float, default=60.0,
                     help="serving: seconds of arrivals (0 = no serving run)")
