@@ -160,7 +160,13 @@ typedef struct {
     int32_t graph;          /* 0: the depth-first pass loop runs as one CUDA graph launch (a
                                conditional while node; not with a time limit or tracing);
                                -1: the host launches each pass                             */
-    int32_t reserved;
+    int32_t engine;         /* 0: the canonical ridge-driven search; 1: the GF(2) cycle-space
+                               sweep of Section 2.1 (all 2^s elements of ker_Z2 A in Gray-code
+                               order, checked by Proposition 2.1): maps with M <= 256, N <=
+                               1024 and s <= sweep_max_s, else WPM_ERR_LIMIT. Same counts and
+                               lists; `nodes` then counts kernel elements visited, `probes` 0 */
+    int32_t sweep_max_s;    /* largest kernel dimension the sweep accepts (0 = 30, max 48)  */
+    int32_t reserved[2];
 } wpm_tuning;
 
 /* Statistics of the calling thread's last enumeration run. */

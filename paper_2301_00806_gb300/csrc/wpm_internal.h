@@ -151,6 +151,24 @@ struct PassArgs {
 // Park record header words (before the item words of the parked node).
 constexpr int kParkHeader = 4;  // valid, top entry, depth | base << 16, unused
 
+// GF(2) cycle-space sweep (wpm_sweep.cu): maps with M <= kSweepMaxM candidate facets and
+// N <= kSweepMaxN ridges; kernel bases of dimension up to kSweepMaxS are stored.
+constexpr int kSweepW = 4;          // u64 words of a facet set
+constexpr int kSweepMaxM = 64 * kSweepW;
+constexpr int kSweepMaxN = 1024;
+constexpr int kSweepMaxS = 48;
+// Basis of ker A over GF(2) for maps ids[0..n_ids): basis[j] holds kSweepMaxS vectors of
+// kSweepW words, dims[j] the dimension (vectors stored only when it is <= kSweepMaxS).
+cudaError_t launch_kernel_basis(const InstDesc *d_inst, const int32_t *d_ids, int n_ids,
+                                int max_n_ridges, uint64_t *basis, int32_t *dims, cudaStream_t s);
+// All 2^dims[j] combinations of map j, in chunks of 2^clogs[j] Gray-code steps; chunks is the
+// exclusive prefix of the chunk counts (n_ids + 1 entries, the last = total_chunks).
+cudaError_t launch_sweep(const InstDesc *d_inst, const int32_t *d_ids, int n_ids,
+                         const uint64_t *basis, const int32_t *dims, const int32_t *clogs,
+                         const unsigned long long *chunks, unsigned long long total_chunks,
+                         int max_n_ridges, const OutDesc *outs, unsigned long long *ctr,
+                         cudaStream_t s);
+
 // Launchers (wpm_kernels.cu). All return cudaError_t of the launch.
 // One-thread kernels of a graph-driven pass loop: prep makes the items left by the last pass
 // this pass's and clears the pass counters; check sets the loop's condition h.

@@ -69,16 +69,18 @@ struct Workspace {
   cudaStream_t own = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   PassGraph pg;
-  DevBuf inst, outd, ctr, arena, cond, ids, q, ring, ready, stack, aff, park, out, seg, segs, stage;
-  PinBuf h_inst, h_outd, h_q, h_ctr, h_cond, h_ids, h_seg, h_segs, h_stage;
+  DevBuf inst, outd, ctr, arena, cond, ids, q, ring, ready, stack, aff, park, out, seg, segs, stage,
+      sweep;
+  PinBuf h_inst, h_outd, h_q, h_ctr, h_cond, h_ids, h_seg, h_segs, h_stage, h_sweep;
   void release() {
     pg.reset();
     if (pg.capture) cudaStreamDestroy(pg.capture);
     pg.capture = nullptr;
     for (DevBuf *b : {&inst, &outd, &ctr, &arena, &cond, &ids, &q, &ring, &ready, &stack, &aff, &park, &out, &seg,
-                      &segs, &stage})
+                      &segs, &stage, &sweep})
       b->release();
-    for (PinBuf *b : {&h_inst, &h_outd, &h_q, &h_ctr, &h_cond, &h_ids, &h_seg, &h_segs, &h_stage})
+    for (PinBuf *b : {&h_inst, &h_outd, &h_q, &h_ctr, &h_cond, &h_ids, &h_seg, &h_segs, &h_stage,
+                      &h_sweep})
       b->release();
   }
 };
@@ -206,6 +208,8 @@ struct RunOptions {
   int donate_levels = 0;
   int donate_every = 0;
   int graph = 0;  // < 0: host-driven pass loop
+  int engine = 0;  // 1: GF(2) cycle-space sweep
+  int sweep_max_s = 0;
   long long hungry_items = 0;
   bool profile = false;
   bool setup_only = false;  // stop after the setup kernel (candidate facets)
@@ -292,6 +296,57 @@ static cudaError_t launch_pass_graph(Workspace *W, const PassArgs &pa, int k, in
     G.tpb = tpb;
   }
   return cudaGraphLaunch(G.exec, s);
+}
+
+// The GF(2) cycle-space sweep over the valid instances (their ids are in W->ids): a kernel
+// basis per map, then every element of the kernel in Gray-code order (wpm_sweep.cu). Counts
+// and list-mode masks land in the same counters and output regions as the search's.
+static int run_sweep(Workspace *W, const InstDesc *hd, const std::vector<int32_t> &valid,
+                     int max_s, cudaStream_t s) {
+  const int nv = (int)valid.size();
+  max_s = max_s > 0 ? std::min(max_s, kSweepMaxS) : 30;
+  int max_n_ridges = 1;
+  for (int i : valid) {
+    if (hd[i].M > kSweepMaxM || hd[i].N > kSweepMaxN)
+      return fail(WPM_ERR_LIMIT, "sweep: instance %d has M=%d, N=%d (the sweep takes M <= %d, "
+                  "N <= %d)", i, hd[i].M, hd[i].N, kSweepMaxM, kSweepMaxN);
+    max_n_ridges = std::max(max_n_ridges, hd[i].N);
+  }
+  const size_t basis_bytes = align_up(8ull * nv * kSweepMaxS * kSweepW);
+  const size_t dims_bytes = align_up(4ull * nv);
+  const size_t chunk_bytes = align_up(8ull * (nv + 1));
+  WPM_TRY(W->sweep.ensure(basis_bytes + 2 * dims_bytes + chunk_bytes));
+  WPM_TRY(W->h_sweep.ensure(2 * dims_bytes + chunk_bytes));
+  char *db = W->sweep.as<char>();
+  uint64_t *basis = (uint64_t *)db;
+  int32_t *dims = (int32_t *)(db + basis_bytes);
+  int32_t *clogs = (int32_t *)(db + basis_bytes + dims_bytes);
+  unsigned long long *chunks = (unsigned long long *)(db + basis_bytes + 2 * dims_bytes);
+  char *hb = W->h_sweep.as<char>();
+  int32_t *hdims = (int32_t *)hb;
+  int32_t *hclogs = (int32_t *)(hb + dims_bytes);
+  unsigned long long *hchunks = (unsigned long long *)(hb + 2 * dims_bytes);
+  CUDA_TRY(launch_kernel_basis(W->inst.as<InstDesc>(), W->ids.as<int32_t>(), nv, max_n_ridges,
+                               basis, dims, s));
+  t_stats.kernel_launches++;
+  CUDA_TRY(cudaMemcpyAsync(hdims, dims, 4ull * nv, cudaMemcpyDeviceToHost, s));
+  count_copy(hdims, dims, 4ull * nv, cudaMemcpyDeviceToHost);
+  CUDA_TRY(cudaStreamSynchronize(s));
+  hchunks[0] = 0;
+  for (int j = 0; j < nv; j++) {
+    if (hdims[j] > max_s)
+      return fail(WPM_ERR_LIMIT, "sweep: instance %d has a kernel of dimension %d (limit %d)",
+                  valid[j], hdims[j], max_s);
+    hclogs[j] = std::min(hdims[j], 12);  // chunks of 4096 Gray-code steps
+    hchunks[j + 1] = hchunks[j] + (1ull << (hdims[j] - hclogs[j]));
+  }
+  CUDA_TRY(cudaMemcpyAsync(clogs, hclogs, dims_bytes + chunk_bytes, cudaMemcpyHostToDevice, s));
+  count_copy(clogs, hclogs, dims_bytes + chunk_bytes, cudaMemcpyHostToDevice);
+  CUDA_TRY(launch_sweep(W->inst.as<InstDesc>(), W->ids.as<int32_t>(), nv, basis, dims, clogs,
+                        chunks, hchunks[nv], max_n_ridges, W->outd.as<OutDesc>(),
+                        W->ctr.as<unsigned long long>(), s));
+  t_stats.kernel_launches++;
+  return WPM_OK;
 }
 
 // The engine of every entry point: run the instances `hi` on stream `s`.
@@ -498,200 +553,206 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
   for (int j = 0; j < n_valid; j++) hids[j] = valid[j];
   CUDA_TRY(cudaMemcpyAsync(W->ids.p, hids, 4ull * n_valid, cudaMemcpyHostToDevice, s));
   count_copy(W->ids.p, hids, 4ull * n_valid, cudaMemcpyHostToDevice);
-  QueueCtl *hq = W->h_q.as<QueueCtl>();
-  memset(hq, 0, sizeof(QueueCtl));
-  CUDA_TRY(cudaMemcpyAsync(W->q.p, hq, sizeof(QueueCtl), cudaMemcpyHostToDevice, s));
-  count_copy(W->q.p, hq, sizeof(QueueCtl), cudaMemcpyHostToDevice);
-  t_stats.kernel_launches++;
-  CUDA_TRY(launch_roots(W->inst.as<InstDesc>(), n_valid, W->ids.as<int32_t>(),
-                        W->ctr.as<unsigned long long>(), W->ring.as<uint32_t>(), ring_cap, iw,
-                        size_class(k).mw, W->q.as<QueueCtl>(), s));
-  CUDA_TRY(cudaMemcpyAsync(hq, W->q.p, sizeof(QueueCtl), cudaMemcpyDeviceToHost, s));
-  count_copy(hq, W->q.p, sizeof(QueueCtl), cudaMemcpyDeviceToHost);
-  CUDA_TRY(cudaStreamSynchronize(s));
-
-  PassArgs pa;
-  memset(&pa, 0, sizeof(pa));  // no parking: every field not set below is zero
-  pa.inst = W->inst.as<InstDesc>();
-  pa.outs = W->outd.as<OutDesc>();
-  pa.ctr = W->ctr.as<unsigned long long>();
-  pa.ring = W->ring.as<uint32_t>();
-  pa.ring_cap = ring_cap;
-  pa.item_words = iw;
-  pa.q = W->q.as<QueueCtl>();
-  pa.max_depth = max_depth;
-  pa.n_threads = n_threads;
-  pa.stack = search == kSearchThread ? W->stack.as<uint32_t>() : nullptr;
-  pa.aff_scratch = search == kSearchThread ? W->aff.as<long long>() : nullptr;
-  pa.budget = budget;
-  pa.dump_limit = dump_limit;
-  pa.park = search == kSearchThread ? W->park.as<uint32_t>() : nullptr;
-  pa.ready = search == kSearchThread ? W->ready.as<uint32_t>() : nullptr;
-  pa.hungry = opt.hungry_items > 0 ? (unsigned long long)opt.hungry_items
-                                    : (unsigned long long)n_searches;
-  pa.feed = opt.feed_levels > 0 ? opt.feed_levels : (opt.feed_levels < 0 ? (1 << 20) : 8);
-  pa.donate = opt.donate_levels > 0 ? opt.donate_levels : (opt.donate_levels < 0 ? 0 : 4);
-  pa.donate_every = opt.donate_every > 0 ? opt.donate_every : 2048;
-  const int idle_pct = (opt.idle_percent > 0 && opt.idle_percent <= 100) ? opt.idle_percent : 20;
-  pa.idle_limit = std::max<unsigned long long>(1, (unsigned long long)n_searches * idle_pct / 100);
-  const bool trace = getenv("WPM_TRACE") != nullptr;
-  pa.trace = trace ? 1 : 0;
-  if (trace)
-    fprintf(stderr, "[wpm] %d instances, class %d (mw %d nw %d), %s search, %d blocks x %d "
-            "threads, budget %lld, ring %llu items of %d words, max depth %d\n", n_valid, k,
-            size_class(k).mw, size_class(k).nw, search == kSearchThread ? "thread" : "warp",
-            blocks, tpb, budget, ring_cap, iw, max_depth);
-  t_stats.search = search;
-  t_stats.size_class = k;
-  t_stats.searches = n_searches;
-  const bool timed = trace || opt.profile;
-  if (timed && !W->ev0) {
-    CUDA_TRY(cudaEventCreate(&W->ev0));
-    CUDA_TRY(cudaEventCreate(&W->ev1));
-  }
-  cudaEvent_t ev0 = W->ev0, ev1 = W->ev1;
-  int pass_no = 0;
-
-  // ---- breadth-first expansion, then depth-first passes -----------------------------
-  const auto t_start = std::chrono::steady_clock::now();
-  auto out_of_time = [&]() {
-    if (opt.time_limit_ms <= 0) return false;
-    const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(
-                        std::chrono::steady_clock::now() - t_start).count();
-    return ms >= opt.time_limit_ms;
-  };
   bool timed_out = false;
-  unsigned long long head = 0, tail = hq->tail;
-  for (;;) {
-    const unsigned long long live = tail - head;
-    if (live == 0 || (long long)live >= frontier_target) break;
-    if (live * (unsigned long long)max_children + live > ring_cap) break;  // children must fit
-    hq->head = tail;
-    hq->tail = tail;
-    hq->limit = tail;
-    hq->head_start = head;
-    hq->err = 0;
-    hq->idle = 0;
-    hq->nodes = 0;
-    CUDA_TRY(cudaMemcpyAsync(W->q.p, hq, sizeof(QueueCtl), cudaMemcpyHostToDevice, s));
-  count_copy(W->q.p, hq, sizeof(QueueCtl), cudaMemcpyHostToDevice);
-    if (timed) CUDA_TRY(cudaEventRecord(ev0, s));
-    CUDA_TRY(launch_expand(k, pa, (int)live, 256, s));
-    if (timed) CUDA_TRY(cudaEventRecord(ev1, s));
-    t_stats.kernel_launches++;
-    t_stats.expand_passes++;
-    CUDA_TRY(cudaMemcpyAsync(hq, W->q.p, sizeof(QueueCtl), cudaMemcpyDeviceToHost, s));
-  count_copy(hq, W->q.p, sizeof(QueueCtl), cudaMemcpyDeviceToHost);
-    CUDA_TRY(cudaStreamSynchronize(s));
-    if (hq->err) return fail(WPM_ERR_NOMEM, "work ring overflow during expansion");
-    float ms = 0;
-    if (timed) {
-      CUDA_TRY(cudaEventElapsedTime(&ms, ev0, ev1));
-      t_stats.expand_ms += ms;
-    }
-    if (trace) {
-      fprintf(stderr, "[wpm] expand %d: %llu items -> %llu items, %.3f ms\n", pass_no++, live,
-              hq->tail - tail, ms);
-    }
-    head = tail;
-    tail = hq->tail;
-  }
-  unsigned long long parked = 0;  // searches that parked work in the last pass
-  unsigned long long epoch = 0;   // ready-flag stamp of the last pass (the flags were zeroed)
-  // Without tracing or a time limit the pass loop runs on the device: one graph launch, whose
-  // conditional while node repeats prep, pass and check until no item or parked search is
-  // left (no host round trip between passes).
-  if (tail > head && !trace && opt.time_limit_ms <= 0 && opt.graph >= 0) {
+  if (opt.engine == 1) {
+    WPM_TRY(run_sweep(W, hd, valid, opt.sweep_max_s, s));
+    t_stats.search = 0;
+  } else {
+    QueueCtl *hq = W->h_q.as<QueueCtl>();
     memset(hq, 0, sizeof(QueueCtl));
-    hq->head = head;
-    hq->tail = tail;
-    hq->limit = tail;
-    hq->head_start = head;
     CUDA_TRY(cudaMemcpyAsync(W->q.p, hq, sizeof(QueueCtl), cudaMemcpyHostToDevice, s));
     count_copy(W->q.p, hq, sizeof(QueueCtl), cudaMemcpyHostToDevice);
-    if (timed) CUDA_TRY(cudaEventRecord(ev0, s));
-    const cudaError_t ge = launch_pass_graph(W, pa, k, search, blocks, tpb, s);
-    if (ge == cudaSuccess) {
+    t_stats.kernel_launches++;
+    CUDA_TRY(launch_roots(W->inst.as<InstDesc>(), n_valid, W->ids.as<int32_t>(),
+                          W->ctr.as<unsigned long long>(), W->ring.as<uint32_t>(), ring_cap, iw,
+                          size_class(k).mw, W->q.as<QueueCtl>(), s));
+    CUDA_TRY(cudaMemcpyAsync(hq, W->q.p, sizeof(QueueCtl), cudaMemcpyDeviceToHost, s));
+    count_copy(hq, W->q.p, sizeof(QueueCtl), cudaMemcpyDeviceToHost);
+    CUDA_TRY(cudaStreamSynchronize(s));
+
+    PassArgs pa;
+    memset(&pa, 0, sizeof(pa));  // no parking: every field not set below is zero
+    pa.inst = W->inst.as<InstDesc>();
+    pa.outs = W->outd.as<OutDesc>();
+    pa.ctr = W->ctr.as<unsigned long long>();
+    pa.ring = W->ring.as<uint32_t>();
+    pa.ring_cap = ring_cap;
+    pa.item_words = iw;
+    pa.q = W->q.as<QueueCtl>();
+    pa.max_depth = max_depth;
+    pa.n_threads = n_threads;
+    pa.stack = search == kSearchThread ? W->stack.as<uint32_t>() : nullptr;
+    pa.aff_scratch = search == kSearchThread ? W->aff.as<long long>() : nullptr;
+    pa.budget = budget;
+    pa.dump_limit = dump_limit;
+    pa.park = search == kSearchThread ? W->park.as<uint32_t>() : nullptr;
+    pa.ready = search == kSearchThread ? W->ready.as<uint32_t>() : nullptr;
+    pa.hungry = opt.hungry_items > 0 ? (unsigned long long)opt.hungry_items
+                                      : (unsigned long long)n_searches;
+    pa.feed = opt.feed_levels > 0 ? opt.feed_levels : (opt.feed_levels < 0 ? (1 << 20) : 8);
+    pa.donate = opt.donate_levels > 0 ? opt.donate_levels : (opt.donate_levels < 0 ? 0 : 4);
+    pa.donate_every = opt.donate_every > 0 ? opt.donate_every : 2048;
+    const int idle_pct = (opt.idle_percent > 0 && opt.idle_percent <= 100) ? opt.idle_percent : 20;
+    pa.idle_limit = std::max<unsigned long long>(1, (unsigned long long)n_searches * idle_pct / 100);
+    const bool trace = getenv("WPM_TRACE") != nullptr;
+    pa.trace = trace ? 1 : 0;
+    if (trace)
+      fprintf(stderr, "[wpm] %d instances, class %d (mw %d nw %d), %s search, %d blocks x %d "
+              "threads, budget %lld, ring %llu items of %d words, max depth %d\n", n_valid, k,
+              size_class(k).mw, size_class(k).nw, search == kSearchThread ? "thread" : "warp",
+              blocks, tpb, budget, ring_cap, iw, max_depth);
+    t_stats.search = search;
+    t_stats.size_class = k;
+    t_stats.searches = n_searches;
+    const bool timed = trace || opt.profile;
+    if (timed && !W->ev0) {
+      CUDA_TRY(cudaEventCreate(&W->ev0));
+      CUDA_TRY(cudaEventCreate(&W->ev1));
+    }
+    cudaEvent_t ev0 = W->ev0, ev1 = W->ev1;
+    int pass_no = 0;
+
+    // ---- breadth-first expansion, then depth-first passes -----------------------------
+    const auto t_start = std::chrono::steady_clock::now();
+    auto out_of_time = [&]() {
+      if (opt.time_limit_ms <= 0) return false;
+      const auto ms = std::chrono::duration_cast<std::chrono::milliseconds>(
+                          std::chrono::steady_clock::now() - t_start).count();
+      return ms >= opt.time_limit_ms;
+    };
+    timed_out = false;
+    unsigned long long head = 0, tail = hq->tail;
+    for (;;) {
+      const unsigned long long live = tail - head;
+      if (live == 0 || (long long)live >= frontier_target) break;
+      if (live * (unsigned long long)max_children + live > ring_cap) break;  // children must fit
+      hq->head = tail;
+      hq->tail = tail;
+      hq->limit = tail;
+      hq->head_start = head;
+      hq->err = 0;
+      hq->idle = 0;
+      hq->nodes = 0;
+      CUDA_TRY(cudaMemcpyAsync(W->q.p, hq, sizeof(QueueCtl), cudaMemcpyHostToDevice, s));
+    count_copy(W->q.p, hq, sizeof(QueueCtl), cudaMemcpyHostToDevice);
+      if (timed) CUDA_TRY(cudaEventRecord(ev0, s));
+      CUDA_TRY(launch_expand(k, pa, (int)live, 256, s));
       if (timed) CUDA_TRY(cudaEventRecord(ev1, s));
+      t_stats.kernel_launches++;
+      t_stats.expand_passes++;
       CUDA_TRY(cudaMemcpyAsync(hq, W->q.p, sizeof(QueueCtl), cudaMemcpyDeviceToHost, s));
-      count_copy(hq, W->q.p, sizeof(QueueCtl), cudaMemcpyDeviceToHost);
+    count_copy(hq, W->q.p, sizeof(QueueCtl), cudaMemcpyDeviceToHost);
+      CUDA_TRY(cudaStreamSynchronize(s));
+      if (hq->err) return fail(WPM_ERR_NOMEM, "work ring overflow during expansion");
+      float ms = 0;
+      if (timed) {
+        CUDA_TRY(cudaEventElapsedTime(&ms, ev0, ev1));
+        t_stats.expand_ms += ms;
+      }
+      if (trace) {
+        fprintf(stderr, "[wpm] expand %d: %llu items -> %llu items, %.3f ms\n", pass_no++, live,
+                hq->tail - tail, ms);
+      }
+      head = tail;
+      tail = hq->tail;
+    }
+    unsigned long long parked = 0;  // searches that parked work in the last pass
+    unsigned long long epoch = 0;   // ready-flag stamp of the last pass (the flags were zeroed)
+    // Without tracing or a time limit the pass loop runs on the device: one graph launch, whose
+    // conditional while node repeats prep, pass and check until no item or parked search is
+    // left (no host round trip between passes).
+    if (tail > head && !trace && opt.time_limit_ms <= 0 && opt.graph >= 0) {
+      memset(hq, 0, sizeof(QueueCtl));
+      hq->head = head;
+      hq->tail = tail;
+      hq->limit = tail;
+      hq->head_start = head;
+      CUDA_TRY(cudaMemcpyAsync(W->q.p, hq, sizeof(QueueCtl), cudaMemcpyHostToDevice, s));
+      count_copy(W->q.p, hq, sizeof(QueueCtl), cudaMemcpyHostToDevice);
+      if (timed) CUDA_TRY(cudaEventRecord(ev0, s));
+      const cudaError_t ge = launch_pass_graph(W, pa, k, search, blocks, tpb, s);
+      if (ge == cudaSuccess) {
+        if (timed) CUDA_TRY(cudaEventRecord(ev1, s));
+        CUDA_TRY(cudaMemcpyAsync(hq, W->q.p, sizeof(QueueCtl), cudaMemcpyDeviceToHost, s));
+        count_copy(hq, W->q.p, sizeof(QueueCtl), cudaMemcpyDeviceToHost);
+        CUDA_TRY(cudaStreamSynchronize(s));
+        if (hq->err & 1ull) return fail(WPM_ERR_NOMEM, "work ring overflow (raise ring_items)");
+        if (hq->err & 2ull) return fail(WPM_ERR_LIMIT, "search stack overflow");
+        if (hq->err & 4ull) return fail(WPM_ERR_CUDA, "a work item was never published");
+        if (hq->err & 8ull) return fail(WPM_ERR_CUDA, "pass loop did not finish");
+        t_stats.dfs_passes += hq->passes;
+        t_stats.kernel_launches += 3 * hq->passes;
+        t_stats.graph_launches++;
+        if (timed) {
+          float ms = 0;
+          CUDA_TRY(cudaEventElapsedTime(&ms, ev0, ev1));
+          t_stats.dfs_ms += ms;
+        }
+        head = tail = 0;  // all done
+      } else if (ge != cudaErrorNotSupported) {
+        return fail(WPM_ERR_CUDA, "pass graph: %s", cudaGetErrorString(ge));
+      }
+    }
+    while (tail > head || parked > 0) {
+      if (out_of_time()) {
+        timed_out = true;
+        break;
+      }
+      hq->head = head;
+      hq->tail = tail;
+      hq->limit = tail;
+      hq->head_start = head;
+      hq->err = 0;
+      hq->idle = 0;
+      hq->nodes = 0;
+      hq->parked = 0;
+      hq->iters = hq->lanes_step = hq->lanes_fetch = hq->lanes_dump = hq->lanes_stopped = 0;
+      hq->waiting = hq->exited = hq->full = 0;
+      hq->epoch = ++epoch;
+      if (opt.time_limit_ms > 0) {  // a long pass ends by itself when the time is up
+        const long long used = std::chrono::duration_cast<std::chrono::nanoseconds>(
+                                   std::chrono::steady_clock::now() - t_start).count();
+        pa.time_left_ns = (unsigned long long)std::max<long long>(
+            1, (long long)opt.time_limit_ms * 1000000ll - used);
+      }
+      CUDA_TRY(cudaMemcpyAsync(W->q.p, hq, sizeof(QueueCtl), cudaMemcpyHostToDevice, s));
+    count_copy(W->q.p, hq, sizeof(QueueCtl), cudaMemcpyHostToDevice);
+      if (timed) CUDA_TRY(cudaEventRecord(ev0, s));
+      CUDA_TRY(launch_dfs(k, search, pa, blocks, tpb, s));
+      if (timed) CUDA_TRY(cudaEventRecord(ev1, s));
+      t_stats.kernel_launches++;
+      t_stats.dfs_passes++;
+      CUDA_TRY(cudaMemcpyAsync(hq, W->q.p, sizeof(QueueCtl), cudaMemcpyDeviceToHost, s));
+    count_copy(hq, W->q.p, sizeof(QueueCtl), cudaMemcpyDeviceToHost);
       CUDA_TRY(cudaStreamSynchronize(s));
       if (hq->err & 1ull) return fail(WPM_ERR_NOMEM, "work ring overflow (raise ring_items)");
       if (hq->err & 2ull) return fail(WPM_ERR_LIMIT, "search stack overflow");
       if (hq->err & 4ull) return fail(WPM_ERR_CUDA, "a work item was never published");
-      if (hq->err & 8ull) return fail(WPM_ERR_CUDA, "pass loop did not finish");
-      t_stats.dfs_passes += hq->passes;
-      t_stats.kernel_launches += 3 * hq->passes;
-      t_stats.graph_launches++;
+      // per-thread passes also take items written during the pass (their head never passes
+      // the tail); per-warp passes take only items that were there when it began
+      const unsigned long long taken_to =
+          search == kSearchThread ? std::min(hq->head, hq->tail) : std::min(hq->head, tail);
+      t_stats.items += taken_to - head;
+      float ms = 0;
       if (timed) {
-        float ms = 0;
         CUDA_TRY(cudaEventElapsedTime(&ms, ev0, ev1));
         t_stats.dfs_ms += ms;
       }
-      head = tail = 0;  // all done
-    } else if (ge != cudaErrorNotSupported) {
-      return fail(WPM_ERR_CUDA, "pass graph: %s", cudaGetErrorString(ge));
+      if (trace) {
+        fprintf(stderr, "[wpm] dfs %d: %llu items, %llu taken, %llu new, %llu parked, %llu nodes, "
+                "%.3f ms", pass_no++, tail - head, taken_to - head, hq->tail - tail, hq->parked,
+                hq->nodes, ms);
+        if (hq->iters)
+          fprintf(stderr, "; warp iterations %llu, lanes/iteration: step %.2f fetch %.3f stopped "
+                  "%.2f; dumps %llu", hq->iters, (double)hq->lanes_step / hq->iters,
+                  (double)hq->lanes_fetch / hq->iters, (double)hq->lanes_stopped / hq->iters,
+                  hq->lanes_dump);
+        fprintf(stderr, "\n");
+      }
+      head = taken_to;
+      tail = hq->tail;
+      parked = hq->parked;
     }
-  }
-  while (tail > head || parked > 0) {
-    if (out_of_time()) {
-      timed_out = true;
-      break;
-    }
-    hq->head = head;
-    hq->tail = tail;
-    hq->limit = tail;
-    hq->head_start = head;
-    hq->err = 0;
-    hq->idle = 0;
-    hq->nodes = 0;
-    hq->parked = 0;
-    hq->iters = hq->lanes_step = hq->lanes_fetch = hq->lanes_dump = hq->lanes_stopped = 0;
-    hq->waiting = hq->exited = hq->full = 0;
-    hq->epoch = ++epoch;
-    if (opt.time_limit_ms > 0) {  // a long pass ends by itself when the time is up
-      const long long used = std::chrono::duration_cast<std::chrono::nanoseconds>(
-                                 std::chrono::steady_clock::now() - t_start).count();
-      pa.time_left_ns = (unsigned long long)std::max<long long>(
-          1, (long long)opt.time_limit_ms * 1000000ll - used);
-    }
-    CUDA_TRY(cudaMemcpyAsync(W->q.p, hq, sizeof(QueueCtl), cudaMemcpyHostToDevice, s));
-  count_copy(W->q.p, hq, sizeof(QueueCtl), cudaMemcpyHostToDevice);
-    if (timed) CUDA_TRY(cudaEventRecord(ev0, s));
-    CUDA_TRY(launch_dfs(k, search, pa, blocks, tpb, s));
-    if (timed) CUDA_TRY(cudaEventRecord(ev1, s));
-    t_stats.kernel_launches++;
-    t_stats.dfs_passes++;
-    CUDA_TRY(cudaMemcpyAsync(hq, W->q.p, sizeof(QueueCtl), cudaMemcpyDeviceToHost, s));
-  count_copy(hq, W->q.p, sizeof(QueueCtl), cudaMemcpyDeviceToHost);
-    CUDA_TRY(cudaStreamSynchronize(s));
-    if (hq->err & 1ull) return fail(WPM_ERR_NOMEM, "work ring overflow (raise ring_items)");
-    if (hq->err & 2ull) return fail(WPM_ERR_LIMIT, "search stack overflow");
-    if (hq->err & 4ull) return fail(WPM_ERR_CUDA, "a work item was never published");
-    // per-thread passes also take items written during the pass (their head never passes
-    // the tail); per-warp passes take only items that were there when it began
-    const unsigned long long taken_to =
-        search == kSearchThread ? std::min(hq->head, hq->tail) : std::min(hq->head, tail);
-    t_stats.items += taken_to - head;
-    float ms = 0;
-    if (timed) {
-      CUDA_TRY(cudaEventElapsedTime(&ms, ev0, ev1));
-      t_stats.dfs_ms += ms;
-    }
-    if (trace) {
-      fprintf(stderr, "[wpm] dfs %d: %llu items, %llu taken, %llu new, %llu parked, %llu nodes, "
-              "%.3f ms", pass_no++, tail - head, taken_to - head, hq->tail - tail, hq->parked,
-              hq->nodes, ms);
-      if (hq->iters)
-        fprintf(stderr, "; warp iterations %llu, lanes/iteration: step %.2f fetch %.3f stopped "
-                "%.2f; dumps %llu", hq->iters, (double)hq->lanes_step / hq->iters,
-                (double)hq->lanes_fetch / hq->iters, (double)hq->lanes_stopped / hq->iters,
-                hq->lanes_dump);
-      fprintf(stderr, "\n");
-    }
-    head = taken_to;
-    tail = hq->tail;
-    parked = hq->parked;
   }
 
   // ---- counters ----------------------------------------------------------------------
@@ -835,6 +896,8 @@ static RunOptions options_from(const wpm_tuning *t, int mode) {
     o.donate_levels = t->donate_levels;
     o.donate_every = t->donate_every;
     o.graph = t->graph;
+    o.engine = t->engine;
+    o.sweep_max_s = t->sweep_max_s;
     o.hungry_items = t->hungry_items;
   }
   return o;

@@ -71,7 +71,8 @@ class Tuning(C.Structure):
                 ("ring_items", C.c_int64), ("search", C.c_int32), ("profile", C.c_int32),
                 ("time_limit_ms", C.c_int32), ("feed_levels", C.c_int32),
                 ("hungry_items", C.c_int64), ("donate_levels", C.c_int32),
-                ("donate_every", C.c_int32), ("graph", C.c_int32), ("reserved", C.c_int32)]
+                ("donate_every", C.c_int32), ("graph", C.c_int32), ("engine", C.c_int32),
+                ("sweep_max_s", C.c_int32), ("reserved", C.c_int32 * 2)]
 
 
 class RunStats(C.Structure):
