@@ -196,6 +196,21 @@ def run_paper_table1(stream):
             "rows": rows}
 
 
+def reduce_over_ranks(ms, nodes, launches, world, device):
+    """Whole-job figures of a weak-scaling run: the slowest rank's time (max) and the nodes
+    and launches of all ranks (sum). One rank: the inputs."""
+    if world <= 1:
+        return float(ms), float(nodes), float(launches)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms, nodes, launches], dtype=torch.float64, device=device)
+    mx = t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    sm = t.clone()
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(sm[1]), float(sm[2])
+
+
 def run_ours(args, rank, world):
     import numpy as np
     import torch
@@ -288,17 +303,8 @@ def run_ours(args, rank, world):
         plain = {"value": pn / pdt, "unit": UNIT, "instances": len(smp),
                  "instances_per_s": len(smp) / pdt, "mode": "one wpm_enumerate call per instance"}
 
-    t = torch.tensor([ms, nodes_step * args.steps, float(launches)], dtype=torch.float64,
-                     device="cuda")
-    if world > 1:
-        import torch.distributed as dist
-        mx = t.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = t.clone()
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        ms_all, nodes_all = float(mx[0]), float(sm[1])
-    else:
-        ms_all, nodes_all = ms, float(nodes_step * args.steps)
+    ms_all, nodes_all, _ = reduce_over_ranks(ms, nodes_step * args.steps, launches, world,
+                                             "cuda")
     if rank != 0:
         return None
     clocks = clock.summary()
