@@ -747,7 +747,9 @@ __global__ void __maxnreg__(96) tdfs_kernel(PassArgs a) {
     // One step. Either the top level has a candidate child left (try it: on success add it
     // and push), or the level is done (pop, and remove its parent's child). Both branches
     // meet in one update of the counters and of Out, so the warp's threads diverge only
-    // in choosing the facet and in examining a pushed child.
+    // in choosing the facet and in examining a pushed child. (Passing over a rejected
+    // candidate inside the step was measured slower: each extra table read then stalls the
+    // whole warp.)
     int p = -1;
     if (!(top >> 31)) {
       const uint32_t U = top & 0x7FFFu;
@@ -764,6 +766,7 @@ __global__ void __maxnreg__(96) tdfs_kernel(PassArgs a) {
       if (p >= 0) top = (top & ~0xFFFu) | (uint32_t)(p + 1);
     }
     const bool trying = p >= 0;
+    uint4 fa, fb;
     if (!trying) {
       depth--;
       if (depth == base) {
@@ -777,7 +780,6 @@ __global__ void __maxnreg__(96) tdfs_kernel(PassArgs a) {
       // the child of `top` that is applied: slot cur of its ridge, or facet start - 1
       p = (top >> 31) ? (int)(top & 0xFFF) - 1 : row_at(S.tp0, S.tp1, (top >> 15) & 15);
     }
-    uint4 fa, fb;
     S.facet_row(p, fa, fb);
     if (trying && !S.child_ok(p, fa, fb)) {
       S.probes++;
