@@ -22,6 +22,9 @@
  *   orc_n2_cycle_sets     n = 2 only: a WPM of dimension 1 is a set of vertex-disjoint
  *                         cycles of the candidate graph; counted by graph search.
  *
+ * And the post-filters of Algorithm 4.4 (lines 8-12) on an output K: orc_pic_seed (every
+ * vertex used, so Pic(K) = 4, and the seedness condition of Proposition 3.1).
+ *
  * The canonical tree (the GPU search reproduces it node for node):
  *   root: In = forced-in facets (plus facet {0..n-1} when the base facet is required),
  *         Out = forced-out facets; the root dies if the two meet or a check below fails.
@@ -854,4 +857,72 @@ long orc_n2_cycle_count(int M, const uint16_t *edges)
         cycles_from(adj, s, s, (uint16_t)(1u << s), 1, -1, cy, &nc, cap);
     free(cy);
     return nc;
+}
+
+/* ---------------------------------------------------------------------------------- */
+/* Algorithm 4.4, lines 8-12: the post-filters on each WPM K.                         */
+/*   Pic(K) = (number of vertices of K) - n; K is discarded when Pic(K) < 4, i.e. when  */
+/*   some vertex of [m] (m = n + 4) lies in no facet of K.                            */
+/*   Seedness condition (Proposition 3.1): there is no face {v, w} of K such that every */
+/*   minimal non-face of K contains both v and w or neither.                          */
+/* Faces are the subsets of facets; a minimal non-face is a non-face all of whose     */
+/* subsets with one vertex fewer are faces. Written out over all 2^m vertex subsets.  */
+/* ---------------------------------------------------------------------------------- */
+
+/* 1 when K (k facets given as vertex masks on [m]) uses every vertex and satisfies the
+   seedness condition; 0 otherwise; -1 on bad input. */
+int orc_pic_seed(int n, int m, int k, const uint16_t *kf)
+{
+    if (m < 1 || m > 16 || k < 0 || n < 1) return -1;
+    uint32_t all = (m == 16) ? 0xFFFFu : ((1u << m) - 1u);
+    uint32_t used = 0;
+    for (int i = 0; i < k; i++) used |= kf[i];
+    if (used != all) return 0;                      /* Pic(K) < 4 */
+    uint32_t nsub = 1u << m;
+    char *face = (char *)calloc(nsub, 1);
+    if (!face) return -1;
+    for (uint32_t S = 0; S < nsub; S++)
+        for (int i = 0; i < k; i++)
+            if ((S & ~(uint32_t)kf[i]) == 0) { face[S] = 1; break; }
+    /* split[v][w] = 1 when some minimal non-face contains exactly one of v, w */
+    char split[16][16];
+    memset(split, 0, sizeof(split));
+    for (uint32_t S = 1; S < nsub; S++) {
+        if (face[S]) continue;
+        int minimal = 1;
+        for (int v = 0; v < m && minimal; v++)
+            if (((S >> v) & 1u) && !face[S & ~(1u << v)]) minimal = 0;
+        if (!minimal) continue;
+        for (int v = 0; v < m; v++)
+            for (int w = 0; w < m; w++)
+                if ((((S >> v) & 1u) != 0) != (((S >> w) & 1u) != 0)) split[v][w] = 1;
+    }
+    int seed = 1;
+    for (int v = 0; v < m && seed; v++)
+        for (int w = v + 1; w < m && seed; w++)
+            if (face[(1u << v) | (1u << w)] && !split[v][w]) seed = 0;
+    free(face);
+    return seed;
+}
+
+/* Apply orc_pic_seed to `count` output masks (W words each, facet j at bit j%64 of word
+   j/64, facets[] the M candidate vertex masks): keep[i] = 1 for the kept ones. Returns the
+   number kept, or -1 on bad input. */
+long orc_filter_pic_seed(int n, int m, int M, const uint16_t *facets, const uint64_t *masks,
+                         long count, int W, uint8_t *keep)
+{
+    uint16_t *kf = (uint16_t *)malloc(sizeof(uint16_t) * (M > 0 ? M : 1));
+    if (!kf) return -1;
+    long kept = 0;
+    for (long i = 0; i < count; i++) {
+        int k = 0;
+        for (int j = 0; j < M; j++)
+            if ((masks[i * W + j / 64] >> (j % 64)) & 1ull) kf[k++] = facets[j];
+        int r = orc_pic_seed(n, m, k, kf);
+        if (r < 0) { free(kf); return -1; }
+        keep[i] = (uint8_t)r;
+        kept += r;
+    }
+    free(kf);
+    return kept;
 }

@@ -69,6 +69,10 @@ def lib():
                                                    C.c_uint64]
             L.orc_walk.argtypes = [C.c_int, C.c_int, C.c_int, u16p, C.POINTER(_Cond), C.c_uint64,
                                    C.c_int, u64p, u64p]
+            L.orc_pic_seed.argtypes = [C.c_int, C.c_int, C.c_int, u16p]
+            L.orc_filter_pic_seed.argtypes = [C.c_int, C.c_int, C.c_int, u16p, u64p, C.c_long,
+                                              C.c_int, C.POINTER(C.c_uint8)]
+            L.orc_filter_pic_seed.restype = C.c_long
             L.orc_n2_cycle_sets.argtypes = [C.c_int, u16p, C.c_int]
             L.orc_n2_cycle_sets.restype = C.c_long
             L.orc_n2_cycle_count.argtypes = [C.c_int, u16p]
@@ -236,3 +240,23 @@ def walk(n, m, facets, seed, depth, cap=CAP_NONE):
                           _p(a, C.c_uint64), _p(b, C.c_uint64)), "walk")
     del keep
     return a, b
+
+
+def pic_seed(n, m, facet_masks) -> bool:
+    """Algorithm 4.4 lines 8-12 on one complex K (its facets as vertex masks): True when K
+    uses all m vertices (Pic(K) = 4) and satisfies the seedness condition (Prop. 3.1)."""
+    kf = np.ascontiguousarray(facet_masks, dtype=np.uint16)
+    return bool(_check(lib().orc_pic_seed(n, m, kf.size, _p(kf, C.c_uint16)), "pic_seed"))
+
+
+def filter_pic_seed(n, m, facets, masks):
+    """Keep flags (uint8 array) of orc_pic_seed over output masks (count, W) of a map whose
+    candidate facets are `facets`."""
+    f = np.ascontiguousarray(facets, dtype=np.uint16)
+    mk = np.ascontiguousarray(masks, dtype=np.uint64)
+    count = mk.shape[0]
+    W = mk.shape[1] if mk.ndim == 2 else 1
+    keep = np.zeros(max(count, 1), dtype=np.uint8)
+    _check(lib().orc_filter_pic_seed(n, m, f.size, _p(f, C.c_uint16), _p(mk, C.c_uint64),
+                                     count, W, _p(keep, C.c_uint8)), "filter_pic_seed")
+    return keep[:count]

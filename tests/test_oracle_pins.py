@@ -312,3 +312,77 @@ def test_n11_subtree_golden_file_reproduces():
         c, nodes, probes, _ = O.enumerate_dfs(11, 15, f, cap=O.CAP_UBT, forced_in=a, forced_out=b,
                                               list_mode=False)
         assert (c, nodes, probes) == (int(t[29]), int(t[30]), int(t[31]))
+
+
+# ---------------------------------------------------------------------------------------
+# Algorithm 4.4 lines 8-12: Pic(K) = 4 (every vertex used) and the seedness condition of
+# Proposition 3.1
+# ---------------------------------------------------------------------------------------
+
+TABLE2_LINE13 = {2: 22, 3: 578, 4: 13679, 5: 47012}  # Table 2, |K(n,4)| at line 13
+
+
+@pytest.mark.parametrize("n", sorted(TABLE2_LINE13))
+def test_table2_line13_post_filters(n):
+    total = 0
+    for rows in I.idcm_orbit_reps(n):
+        f = O.candidate_facets("dual", n, n + 4, rows)
+        _, _, _, masks = O.enumerate_dfs(n, n + 4, f, cap=-2, base_facet=True,
+                                         capacity=1 << 17)
+        total += int(O.filter_pic_seed(n, n + 4, f, masks).sum())
+    assert total == TABLE2_LINE13[n]
+
+
+def _mask(vs):
+    return sum(1 << v for v in vs)
+
+
+def test_simplex_boundary_is_not_a_seed():
+    # the boundary of a simplex has one minimal non-face, all its vertices: no edge is split
+    import itertools
+    for n in range(2, 7):
+        facets = [_mask(c) for c in itertools.combinations(range(n + 1), n)]
+        assert O.pic_seed(n, n + 1, facets) is False
+
+
+def _hexagon():
+    return [_mask((i, (i + 1) % 6)) for i in range(6)]
+
+
+def _wedge(facets, v, m):
+    """Wedge (J-construction) at vertex v: v becomes v and a new vertex m; a facet through v
+    takes both, a facet missing v is joined with each of them."""
+    out = []
+    for F in facets:
+        if (F >> v) & 1:
+            out.append(F | (1 << m))
+        else:
+            out += [F | (1 << v), F | (1 << m)]
+    return out
+
+
+def _suspension(facets, m):
+    return [F | (1 << m) for F in facets] + [F | (1 << (m + 1)) for F in facets]
+
+
+def test_hexagon_and_two_triangles_are_seeds():
+    assert O.pic_seed(2, 6, _hexagon()) is True
+    tri = [_mask(e) for e in ((0, 1), (1, 2), (0, 2), (3, 4), (4, 5), (3, 5))]
+    assert O.pic_seed(2, 6, tri) is True
+
+
+def test_a_wedge_is_not_a_seed():
+    # the two vertices a wedge makes from one lie in the same minimal non-faces
+    for v in range(6):
+        assert O.pic_seed(3, 7, _wedge(_hexagon(), v, 6)) is False
+
+
+def test_suspension_keeps_seedness():
+    # the suspension of a seed is a seed (Section 4.4); of a non-seed, a non-seed
+    assert O.pic_seed(3, 8, _suspension(_hexagon(), 6)) is True
+    w = _wedge(_hexagon(), 0, 6)
+    assert O.pic_seed(4, 9, _suspension(w, 7)) is False
+
+
+def test_unused_vertex_fails_pic():
+    assert O.pic_seed(2, 7, _hexagon()) is False
