@@ -91,7 +91,17 @@ typedef struct {
     const int32_t *affine_c0;   /* [n_affine]                                               */
     const int32_t *affine_coef; /* [n_affine * M], row a = coefficients of property a;
                                    |c| <= 2^20                                              */
+    int32_t post_filter;        /* WPM_POST_* flags: filters applied to the found WPMs
+                                   (Algorithm 4.4, lines 8-12); list mode only, m <= 15      */
+    int32_t reserved;
 } wpm_conditions;
+
+/* Post-filters (Algorithm 4.4): keep K only when it uses all m vertices, i.e. Pic(K) =
+   m - n (line 9 discards Pic(K) < 4), and/or when it satisfies the seedness condition of
+   Proposition 3.1 (line 10: no edge {v, w} of K lies, for every minimal non-face of K, in
+   both or in neither). */
+#define WPM_POST_PIC   1
+#define WPM_POST_SEED  2
 
 /*
  * Results of one instance. Fields marked "in" are set by the caller, "out" by the library.

@@ -468,6 +468,8 @@ int wpm_engine_submit(wpm_engine *e, const wpm_instance *inst, int mode, uint64_
   Job *j = new Job();
   int rc = copy_map(inst->lambda_cols, inst->kind, inst->n, inst->m, j->hi);
   if (rc == WPM_OK) rc = copy_conditions(inst->cond, j->hi);
+  if (rc == WPM_OK && j->hi.post)
+    rc = fail(WPM_ERR_INPUT, "engine: post filters are applied by wpm_enumerate_batch only");
   if (rc != WPM_OK) {
     delete j;
     return rc;

@@ -81,7 +81,7 @@ struct HostInst {
   int kind = 0, n = 0, m = 0;
   uint32_t cols[kMaxVertices] = {0};
   std::vector<uint16_t> given;
-  int cap_req = -1, base_req = 0, n_facets_req = -1, n_aff = 0;
+  int cap_req = -1, base_req = 0, n_facets_req = -1, n_aff = 0, post = 0;
   std::vector<uint64_t> fin, fout;
   std::vector<int32_t> c0, coef;
 };

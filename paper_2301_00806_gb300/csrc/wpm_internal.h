@@ -65,6 +65,8 @@ struct InstDesc {
   const uint16_t *given;   // kind 2: the caller's facet list (n_given vertex masks)
   int32_t n_given, pad0;
   // derived (setup kernel)
+  int32_t post;         // WPM_POST_* flags (applied to the sorted list)
+  int32_t pad1;
   int32_t M, N, cap, base_idx;
   int32_t mw, nw, ow, err;
   int64_t aff_bound0[kMaxAffine];  // c0 + sum of the positive coefficients
@@ -168,6 +170,19 @@ cudaError_t launch_sweep(const InstDesc *d_inst, const int32_t *d_ids, int n_ids
                          const unsigned long long *chunks, unsigned long long total_chunks,
                          int max_n_ridges, const OutDesc *outs, unsigned long long *ctr,
                          cudaStream_t s);
+
+// Post-filters of Algorithm 4.4 (wpm_post.cu) over the sorted lists of the instances
+// sid[0..ns) (masks [seg[j], seg[j+1]) of the flat order): keep[g] = 1 for each mask g that
+// passes its instance's WPM_POST_* flags (1 for instances without flags); then each flagged
+// instance's list is compacted in order and its count and fill counters set to the kept
+// number. Maps with m <= kPostMaxM.
+constexpr int kPostMaxM = 15;
+cudaError_t launch_post_filter(const InstDesc *d_inst, const OutDesc *outs, const int32_t *sid,
+                               int ns, const unsigned long long *seg, unsigned long long total,
+                               uint8_t *keep, cudaStream_t s);
+cudaError_t launch_post_compact(const InstDesc *d_inst, const OutDesc *outs, const int32_t *sid,
+                                int ns, const unsigned long long *seg, const uint8_t *keep,
+                                unsigned long long *ctr, cudaStream_t s);
 
 // Launchers (wpm_kernels.cu). All return cudaError_t of the launch.
 // One-thread kernels of a graph-driven pass loop: prep makes the items left by the last pass

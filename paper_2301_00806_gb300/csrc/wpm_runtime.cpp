@@ -70,14 +70,14 @@ struct Workspace {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   PassGraph pg;
   DevBuf inst, outd, ctr, arena, cond, ids, q, ring, ready, stack, aff, park, out, seg, segs, stage,
-      sweep;
+      sweep, keep;
   PinBuf h_inst, h_outd, h_q, h_ctr, h_cond, h_ids, h_seg, h_segs, h_stage, h_sweep;
   void release() {
     pg.reset();
     if (pg.capture) cudaStreamDestroy(pg.capture);
     pg.capture = nullptr;
     for (DevBuf *b : {&inst, &outd, &ctr, &arena, &cond, &ids, &q, &ring, &ready, &stack, &aff, &park, &out, &seg,
-                      &segs, &stage, &sweep})
+                      &segs, &stage, &sweep, &keep})
       b->release();
     for (PinBuf *b : {&h_inst, &h_outd, &h_q, &h_ctr, &h_cond, &h_ids, &h_seg, &h_segs, &h_stage,
                       &h_sweep})
@@ -117,6 +117,9 @@ int copy_conditions(const wpm_conditions *c, HostInst &h) {
   if (c->ubt_cap < -2) return fail(WPM_ERR_INPUT, "ubt_cap %d is not a cap", c->ubt_cap);
   h.cap_req = c->ubt_cap;
   h.base_req = c->require_base_facet ? 1 : 0;
+  if (c->post_filter & ~(WPM_POST_PIC | WPM_POST_SEED))
+    return fail(WPM_ERR_INPUT, "unknown post_filter flags 0x%x", c->post_filter);
+  h.post = c->post_filter;
   if (c->n_affine < 0 || c->n_affine > WPM_MAX_AFFINE)
     return fail(WPM_ERR_INPUT, "n_affine %d outside 0..%d", c->n_affine, WPM_MAX_AFFINE);
   const bool masks = c->forced_in || c->forced_out || c->n_affine > 0;
@@ -389,6 +392,7 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
     for (int v = 0; v < kMaxVertices; v++) d.cols[v] = h.cols[v];
     d.cap_req = h.cap_req;
     d.base_req = h.base_req;
+    d.post = h.post;
     d.n_facets_req = h.n_facets_req;
     d.n_aff = h.n_aff;
     d.nsub = (int)binom(h.m, h.n);
@@ -444,6 +448,10 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
                       d.n_facets_req, d.M);
     } else if (d.err & kErrCapNeedsPic4) {
       r.status = fail(WPM_ERR_INPUT, "instance %d: WPM_CAP_UBT needs m = n + 4", i);
+    } else if (d.post && opt.mode != WPM_MODE_LIST) {
+      r.status = fail(WPM_ERR_INPUT, "instance %d: post filters need list mode", i);
+    } else if (d.post && d.m > kPostMaxM) {
+      r.status = fail(WPM_ERR_LIMIT, "instance %d: post filters take m <= %d", i, kPostMaxM);
     } else if (d.kind != 2 && d.M == 0) {
       r.status = fail(WPM_ERR_INPUT, "instance %d: the map has rank below %d (no candidate facet)",
                       i, d.kind == 0 ? d.n : d.m - d.n);
@@ -817,6 +825,24 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
                               W->seg.as<unsigned long long>(), total, 1ull << 62, 1, s));
     t_stats.kernel_launches++;
     t_stats.sort_passes++;
+  }
+
+  // ---- post-filters (Algorithm 4.4, lines 8-12) on the sorted lists ---------------------
+  bool any_post = false;
+  for (int i : sorted_ids) any_post |= hd[i].post != 0;
+  if (any_post) {
+    WPM_TRY(W->keep.ensure(total + 256));
+    CUDA_TRY(launch_post_filter(W->inst.as<InstDesc>(), W->outd.as<OutDesc>(), d_sid, ns,
+                                W->seg.as<unsigned long long>(), total, W->keep.as<uint8_t>(), s));
+    CUDA_TRY(launch_post_compact(W->inst.as<InstDesc>(), W->outd.as<OutDesc>(), d_sid, ns,
+                                 W->seg.as<unsigned long long>(), W->keep.as<uint8_t>(),
+                                 W->ctr.as<unsigned long long>(), s));
+    t_stats.kernel_launches += 2;
+    CUDA_TRY(cudaMemcpyAsync(hc2, W->ctr.p, 8ull * kCtrN * n_inst, cudaMemcpyDeviceToHost, s));
+    count_copy(hc2, W->ctr.p, 8ull * kCtrN * n_inst, cudaMemcpyDeviceToHost);
+    CUDA_TRY(cudaStreamSynchronize(s));
+    for (int i : sorted_ids)
+      if (hd[i].post) res[i].count = hc2[kCtrN * i + kCtrCount];
   }
 
   // ---- copy-out -------------------------------------------------------------------------

@@ -48,7 +48,11 @@ class Conditions(C.Structure):
     _fields_ = [("ubt_cap", C.c_int32), ("require_base_facet", C.c_int32),
                 ("n_facets", C.c_int32), ("forced_in", C.POINTER(C.c_uint64)),
                 ("forced_out", C.POINTER(C.c_uint64)), ("n_affine", C.c_int32),
-                ("affine_c0", C.POINTER(C.c_int32)), ("affine_coef", C.POINTER(C.c_int32))]
+                ("affine_c0", C.POINTER(C.c_int32)), ("affine_coef", C.POINTER(C.c_int32)),
+                ("post_filter", C.c_int32), ("reserved", C.c_int32)]
+
+POST_PIC = 1   # keep WPMs that use all m vertices (Pic(K) = m - n)
+POST_SEED = 2  # keep WPMs that satisfy the seedness condition
 
 
 class Output(C.Structure):
@@ -149,10 +153,11 @@ class _Keep:
 
 
 def _conditions(cap=CAP_NONE, base_facet=False, n_facets=0, forced_in=None, forced_out=None,
-                affine=None, keep: Optional[_Keep] = None) -> Conditions:
+                affine=None, keep: Optional[_Keep] = None, post_filter=0) -> Conditions:
     keep = keep or _Keep()
     c = Conditions()
     c.ubt_cap = cap
+    c.post_filter = post_filter
     c.require_base_facet = 1 if base_facet else 0
     c.n_facets = n_facets
     W = max(1, (n_facets + 63) // 64)
@@ -224,11 +229,13 @@ def _run_single(call, list_mode: bool, capacity: int) -> Result:
 
 def enumerate(kind, n: int, m: int, cols: Sequence[int], cap=CAP_NONE, base_facet=False,
               forced_in=None, forced_out=None, affine=None, n_facets=0, list_mode=True,
-              capacity: int = 1 << 14) -> Result:
-    """wpm_enumerate: all WPMs of one map. forced masks / affine rows need n_facets = M."""
+              capacity: int = 1 << 14, post_filter: int = 0) -> Result:
+    """wpm_enumerate: all WPMs of one map. forced masks / affine rows need n_facets = M;
+    post_filter: POST_PIC | POST_SEED (list mode)."""
     keep = _Keep()
     cc = keep.add(np.asarray(cols, dtype=np.uint32))
-    cond = _conditions(cap, base_facet, n_facets, forced_in, forced_out, affine, keep)
+    cond = _conditions(cap, base_facet, n_facets, forced_in, forced_out, affine, keep,
+                       post_filter)
     mode = MODE_LIST if list_mode else MODE_COUNT
     return _run_single(lambda o: lib().wpm_enumerate(_p(cc, C.c_uint32), _KIND[kind], n, m,
                                                      C.byref(cond), C.byref(o), mode),
@@ -262,6 +269,7 @@ class BatchSpec:
     forced_out: object = None
     affine: object = None
     n_facets: int = 0
+    post_filter: int = 0
 
 
 def enumerate_batch(specs: List[BatchSpec], list_mode=True, capacities=None, tuning=None,
@@ -283,7 +291,7 @@ def enumerate_batch(specs: List[BatchSpec], list_mode=True, capacities=None, tun
         s = specs[i]
         cc = keep.add(np.asarray(s.cols, dtype=np.uint32))
         cond = _conditions(s.cap, s.base_facet, s.n_facets, s.forced_in, s.forced_out, s.affine,
-                           keep)
+                           keep, s.post_filter)
         conds.append(cond)
         insts[i].kind = _KIND[s.kind]
         insts[i].n = s.n
