@@ -86,7 +86,7 @@ def build(force: bool = False, checked: bool = False, verbose: bool = False) -> 
     if force or todo or not os.path.exists(lib) or \
             os.path.getmtime(lib) < max(os.path.getmtime(o) for o in objs):
         tmp = lib + f".tmp{os.getpid()}"
-        cmd = [nvcc] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs
+        cmd = [nvcc] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs + ["-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")

@@ -19,6 +19,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -887,11 +888,31 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
   if (sw) CUDA_TRY(cudaMemcpyAsync(W->h_stage.p, W->stage.p, 8 * sw, cudaMemcpyDeviceToHost, s));
   count_copy(W->h_stage.p, W->stage.p, 8 * sw, cudaMemcpyDeviceToHost);
   CUDA_TRY(cudaStreamSynchronize(s));
-  sw = 0;
+  // staging -> the caller's host buffers, split over host threads when there is much to move
+  std::vector<std::pair<size_t, int>> parts;  // (staging word offset, instance)
+  size_t total_words = 0;
   for (int i : host_ids) {
-    const size_t words = res[i].count * (size_t)hd[i].ow;
-    memcpy(outs[i].masks, W->h_stage.as<uint64_t>() + sw, 8 * words);
-    sw += words;
+    parts.emplace_back(total_words, i);
+    total_words += res[i].count * (size_t)hd[i].ow;
+  }
+  auto copy_range = [&](size_t lo, size_t hi) {  // staging words [lo, hi)
+    for (const auto &pi : parts) {
+      const size_t a = pi.first, words = res[pi.second].count * (size_t)hd[pi.second].ow;
+      const size_t x = std::max(a, lo), y = std::min(a + words, hi);
+      if (x < y)
+        memcpy(outs[pi.second].masks + (x - a), W->h_stage.as<uint64_t>() + x, 8 * (y - x));
+    }
+  };
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const size_t n_thr = std::min<size_t>(std::min(16u, hw), 1 + total_words / (1u << 20));
+  if (n_thr <= 1) {
+    copy_range(0, total_words);
+  } else {
+    std::vector<std::thread> th;
+    const size_t per = (total_words + n_thr - 1) / n_thr;
+    for (size_t t = 0; t < n_thr; t++)
+      th.emplace_back(copy_range, t * per, std::min(total_words, (t + 1) * per));
+    for (auto &t : th) t.join();
   }
   return WPM_OK;
 }
