@@ -144,7 +144,8 @@ struct PassArgs {
   // takes a ticket at or past `limit` waits (bounded) for that before reading it. Epochs only
   // grow over the life of the buffer, so stale flags never match.
   uint32_t *ready;                // [ring_cap]
-  int pad3;
+  int small_rows;                 // per-thread passes: every instance has n <= 8 and at most 8
+                                  // parents per ridge (a specialised kernel; 128 threads)
   int donate_every;               // nodes a search searches between two hand-overs
   unsigned long long time_left_ns;  // > 0: searches leave the pass (parking their work) this
                                     // long after it started

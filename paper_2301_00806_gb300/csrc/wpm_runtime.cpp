@@ -596,6 +596,11 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
     pa.dump_limit = dump_limit;
     pa.park = search == kSearchThread ? W->park.as<uint32_t>() : nullptr;
     pa.ready = search == kSearchThread ? W->ready.as<uint32_t>() : nullptr;
+  {
+    bool small = search == kSearchThread;
+    for (int i : valid) small &= hd[i].fstride == 8 && hd[i].pstride == 8;
+    pa.small_rows = small ? 1 : 0;
+  }
     pa.hungry = opt.hungry_items > 0 ? (unsigned long long)opt.hungry_items
                                       : (unsigned long long)n_searches;
     pa.feed = opt.feed_levels > 0 ? opt.feed_levels : (opt.feed_levels < 0 ? (1 << 20) : 8);

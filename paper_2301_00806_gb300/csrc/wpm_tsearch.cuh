@@ -35,9 +35,13 @@
 namespace wpm {
 namespace ts {
 
-template <int MW_, int NW_, int TPB_>
+// kSmall: every instance of the launch has facet rows of at most 8 ridges (n <= 8) and
+// ridges of at most 8 parents, so the second halves of the rows are never read (fewer
+// registers and no predicated upper loops).
+template <int MW_, int NW_, int TPB_, bool SMALL_ = false>
 struct TCls {
   static constexpr int MW = MW_, NW = NW_, TPB = TPB_;
+  static constexpr bool kSmall = SMALL_;
   static constexpr int SW = (NW + 31) / 32;
   static constexpr bool kSummReg = NW <= 64;
   static constexpr int SMW = NW + 2 * MW + (kSummReg ? 0 : SW);
@@ -118,12 +122,12 @@ struct TSearch {
   __device__ __forceinline__ void facet_row(int p, uint4 &a, uint4 &b) {
     const uint4 *row = reinterpret_cast<const uint4 *>(fr + (size_t)p * fstride);
     a = __ldg(row);
-    b = fstride > 8 ? __ldg(row + 1) : make_uint4(0, 0, 0, 0);
+    b = (!K::kSmall && fstride > 8) ? __ldg(row + 1) : make_uint4(0, 0, 0, 0);
   }
   __device__ __forceinline__ void ridge_row(int r, uint4 &a, uint4 &b) {
     const uint4 *row = reinterpret_cast<const uint4 *>(pr + (size_t)r * pstride);
     a = __ldg(row);
-    b = pstride > 8 ? __ldg(row + 1) : make_uint4(kFull, kFull, kFull, kFull);
+    b = (!K::kSmall && pstride > 8) ? __ldg(row + 1) : make_uint4(kFull, kFull, kFull, kFull);
   }
 
   // No ridge of the facet (row a, b) has degree 2; every lookup is issued, none exits early.
@@ -136,7 +140,7 @@ struct TSearch {
         bad |= cnt(r >> 4) >> ((r & 15) * 2);
       }
     }
-    if (n > 8) {
+    if (!K::kSmall && n > 8) {
 #pragma unroll
       for (int k = 8; k < 16; k++) {
         if (k < n) {
@@ -168,7 +172,7 @@ struct TSearch {
         set_summ(w, v);
       }
     }
-    if (n > 8) {
+    if (!K::kSmall && n > 8) {
 #pragma unroll
       for (int k = 8; k < 16; k++) {
         if (k < n) {
@@ -265,7 +269,7 @@ struct TSearch {
         const int q = row_at(na, nb, s);
         if (q != 0xFFFF && !decided(q)) U |= 1u << s;
       }
-      if (pstride > 8) {
+      if (!K::kSmall && pstride > 8) {
 #pragma unroll
         for (int s = 8; s < 15; s++) {
           const int q = row_at(na, nb, s);
@@ -823,9 +827,9 @@ __global__ void __maxnreg__(96) tdfs_kernel(PassArgs a) {
 
 }  // namespace ts
 
-template <int MW, int NW, int TPB>
+template <int MW, int NW, int TPB, bool SMALL = false>
 static cudaError_t tlaunch_t(const PassArgs &a, int grid, size_t smem, cudaStream_t s) {
-  auto fn = ts::tdfs_kernel<ts::TCls<MW, NW, TPB>>;
+  auto fn = ts::tdfs_kernel<ts::TCls<MW, NW, TPB, SMALL>>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   fn<<<grid, TPB, smem, s>>>(a);
