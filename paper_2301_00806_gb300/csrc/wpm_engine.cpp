@@ -290,6 +290,15 @@ int pass(wpm_engine *e) {
   pa.budget = e->budget;
   pa.idle_limit = e->idle_limit;
   pa.dump_limit = e->dump_limit;
+  {  // the row variant the resident jobs allow (m - n + 1 bounds a ridge's parents)
+    int max_n = 0, max_par = 0;
+    for (Job *j : e->slots) {
+      if (!j) continue;
+      max_n = std::max(max_n, j->hi.n);
+      max_par = std::max(max_par, j->hi.m - j->hi.n + 1);
+    }
+    pa.rows = e->tpb == 128 ? rows_variant(max_n, max_par) : 0;
+  }
   pa.park = e->park.as<uint32_t>();
   pa.ready = e->ready.as<uint32_t>();
 

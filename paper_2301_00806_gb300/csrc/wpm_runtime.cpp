@@ -596,10 +596,14 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
     pa.dump_limit = dump_limit;
     pa.park = search == kSearchThread ? W->park.as<uint32_t>() : nullptr;
     pa.ready = search == kSearchThread ? W->ready.as<uint32_t>() : nullptr;
-  {
-    bool small = search == kSearchThread;
-    for (int i : valid) small &= hd[i].fstride == 8 && hd[i].pstride == 8;
-    pa.small_rows = small ? 1 : 0;
+  if (search == kSearchThread) {
+    int max_n = 0;
+    bool few_parents = true;  // every ridge has at most 8 parents (parents rows of 8)
+    for (int i : valid) {
+      max_n = std::max(max_n, hd[i].n);
+      few_parents &= hd[i].pstride == 8;
+    }
+    pa.rows = rows_variant(max_n, few_parents ? 8 : 16);
   }
     pa.hungry = opt.hungry_items > 0 ? (unsigned long long)opt.hungry_items
                                       : (unsigned long long)n_searches;

@@ -35,13 +35,17 @@
 namespace wpm {
 namespace ts {
 
-// kSmall: every instance of the launch has facet rows of at most 8 ridges (n <= 8) and
-// ridges of at most 8 parents, so the second halves of the rows are never read (fewer
-// registers and no predicated upper loops).
-template <int MW_, int NW_, int TPB_, bool SMALL_ = false>
+// ROWS: 0 for any instance; 1 when every instance of the launch has facet rows of at most
+// 8 ridges (n <= 8) and ridges of at most 8 parents, so the second halves of the rows are
+// never read; 2 when facet rows hold at most 12 ridges (n <= 12) and ridges at most 8
+// parents. The variants need fewer registers and run no predicated loop iterations that
+// no instance uses.
+template <int MW_, int NW_, int TPB_, int ROWS_ = 0>
 struct TCls {
   static constexpr int MW = MW_, NW = NW_, TPB = TPB_;
-  static constexpr bool kSmall = SMALL_;
+  static constexpr bool kSmall = ROWS_ == 1;         // rows of 8
+  static constexpr bool kFewParents = ROWS_ != 0;    // parents rows of 8
+  static constexpr int kMaxRidges = ROWS_ == 1 ? 8 : (ROWS_ == 2 ? 12 : 16);
   static constexpr int SW = (NW + 31) / 32;
   static constexpr bool kSummReg = NW <= 64;
   static constexpr int SMW = NW + 2 * MW + (kSummReg ? 0 : SW);
@@ -127,7 +131,7 @@ struct TSearch {
   __device__ __forceinline__ void ridge_row(int r, uint4 &a, uint4 &b) {
     const uint4 *row = reinterpret_cast<const uint4 *>(pr + (size_t)r * pstride);
     a = __ldg(row);
-    b = (!K::kSmall && pstride > 8) ? __ldg(row + 1) : make_uint4(kFull, kFull, kFull, kFull);
+    b = (!K::kFewParents && pstride > 8) ? __ldg(row + 1) : make_uint4(kFull, kFull, kFull, kFull);
   }
 
   // No ridge of the facet (row a, b) has degree 2; every lookup is issued, none exits early.
@@ -142,7 +146,7 @@ struct TSearch {
     }
     if (!K::kSmall && n > 8) {
 #pragma unroll
-      for (int k = 8; k < 16; k++) {
+      for (int k = 8; k < K::kMaxRidges; k++) {
         if (k < n) {
           const int r = row_at(a, b, k);
           bad |= cnt(r >> 4) >> ((r & 15) * 2);
@@ -174,7 +178,7 @@ struct TSearch {
     }
     if (!K::kSmall && n > 8) {
 #pragma unroll
-      for (int k = 8; k < 16; k++) {
+      for (int k = 8; k < K::kMaxRidges; k++) {
         if (k < n) {
           const int r = row_at(a, b, k), w = r >> 4;
           const uint32_t v = cnt(w) + (uint32_t)sign * (1u << ((r & 15) * 2));
@@ -269,7 +273,7 @@ struct TSearch {
         const int q = row_at(na, nb, s);
         if (q != 0xFFFF && !decided(q)) U |= 1u << s;
       }
-      if (!K::kSmall && pstride > 8) {
+      if (!K::kFewParents && pstride > 8) {
 #pragma unroll
         for (int s = 8; s < 15; s++) {
           const int q = row_at(na, nb, s);
@@ -827,9 +831,9 @@ __global__ void __maxnreg__(96) tdfs_kernel(PassArgs a) {
 
 }  // namespace ts
 
-template <int MW, int NW, int TPB, bool SMALL = false>
+template <int MW, int NW, int TPB, int ROWS = 0>
 static cudaError_t tlaunch_t(const PassArgs &a, int grid, size_t smem, cudaStream_t s) {
-  auto fn = ts::tdfs_kernel<ts::TCls<MW, NW, TPB, SMALL>>;
+  auto fn = ts::tdfs_kernel<ts::TCls<MW, NW, TPB, ROWS>>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   fn<<<grid, TPB, smem, s>>>(a);
