@@ -17,6 +17,7 @@ namespace wpm {
     if (mode != 2) return wlaunch_t<mw, nw>(mode, a, grid, n_items, tpb, smem, s);          \
     if (tpb == 128 && a.rows == 1) return tlaunch_t<mw, nw, 128, 1>(a, grid, smem, s);      \
     if (tpb == 128 && a.rows == 2) return tlaunch_t<mw, nw, 128, 2>(a, grid, smem, s);      \
+    if (tpb == 128 && a.rows == 3) return tlaunch_t<mw, nw, 128, 3>(a, grid, smem, s);      \
     if (tpb == 64) return tlaunch_t<mw, nw, 64>(a, grid, smem, s);                          \
     if (tpb == 128) return tlaunch_t<mw, nw, 128>(a, grid, smem, s);                        \
     return tlaunch_t<mw, nw, 256>(a, grid, smem, s);                                        \

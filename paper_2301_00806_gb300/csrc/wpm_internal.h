@@ -144,9 +144,9 @@ struct PassArgs {
   // takes a ticket at or past `limit` waits (bounded) for that before reading it. Epochs only
   // grow over the life of the buffer, so stale flags never match.
   uint32_t *ready;                // [ring_cap]
-  int rows;                       // per-thread passes, 128 threads: 1 when every instance has
-                                  // n <= 8 and at most 8 parents per ridge, 2 when n <= 12 and
-                                  // at most 8 parents (specialised kernels), else 0
+  int rows;                       // per-thread passes, 128 threads: when every instance has
+                                  // at most 8 parents per ridge, 1 for n <= 8, 3 for n <= 9,
+                                  // 2 for n <= 12 (specialised kernels); else 0
   int donate_every;               // nodes a search searches between two hand-overs
   unsigned long long time_left_ns;  // > 0: searches leave the pass (parking their work) this
                                     // long after it started
@@ -190,7 +190,7 @@ cudaError_t launch_post_compact(const InstDesc *d_inst, const OutDesc *outs, con
 // ridge is at most max_parents (m - n + 1 bounds it).
 inline int rows_variant(int max_n, int max_parents) {
   if (max_parents > 8) return 0;
-  return max_n <= 8 ? 1 : (max_n <= 12 ? 2 : 0);
+  return max_n <= 8 ? 1 : (max_n <= 9 ? 3 : (max_n <= 12 ? 2 : 0));
 }
 
 // Launchers (wpm_kernels.cu). All return cudaError_t of the launch.

@@ -35,17 +35,16 @@
 namespace wpm {
 namespace ts {
 
-// ROWS: 0 for any instance; 1 when every instance of the launch has facet rows of at most
-// 8 ridges (n <= 8) and ridges of at most 8 parents, so the second halves of the rows are
-// never read; 2 when facet rows hold at most 12 ridges (n <= 12) and ridges at most 8
-// parents. The variants need fewer registers and run no predicated loop iterations that
-// no instance uses.
+// ROWS: 0 for any instance; otherwise every instance of the launch has ridges of at most 8
+// parents and facet rows of at most 8 ridges (1: n <= 8, the second halves of the rows are
+// never read), 9 ridges (3: n <= 9) or 12 ridges (2: n <= 12). The variants need fewer
+// registers and run no predicated loop iterations that no instance uses.
 template <int MW_, int NW_, int TPB_, int ROWS_ = 0>
 struct TCls {
   static constexpr int MW = MW_, NW = NW_, TPB = TPB_;
   static constexpr bool kSmall = ROWS_ == 1;         // rows of 8
   static constexpr bool kFewParents = ROWS_ != 0;    // parents rows of 8
-  static constexpr int kMaxRidges = ROWS_ == 1 ? 8 : (ROWS_ == 2 ? 12 : 16);
+  static constexpr int kMaxRidges = ROWS_ == 1 ? 8 : (ROWS_ == 3 ? 9 : (ROWS_ == 2 ? 12 : 16));
   static constexpr int SW = (NW + 31) / 32;
   static constexpr bool kSummReg = NW <= 64;
   static constexpr int SMW = NW + 2 * MW + (kSummReg ? 0 : SW);
