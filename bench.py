@@ -43,8 +43,8 @@ UNIT = "nodes/s"
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the depth-first kernel per
 # search node, from one ncu capture of a depth-first launch over 256 maps of this mix
-# (501.7 MB for 2,711,713,518 nodes); the roofline's traffic scales it by the step's nodes.
-TDFS_DRAM_BYTES_PER_NODE = 501.7e6 / 2711713518
+# (410.7 MB for 2,711,713,518 nodes); the roofline's traffic scales it by the step's nodes.
+TDFS_DRAM_BYTES_PER_NODE = 410.7e6 / 2711713518
 
 
 # ------------------------------------------------------------------------------------------
@@ -235,6 +235,8 @@ def run_ours(args, rank, world):
     tuned, tune_ms = wpm.autotune(specs, stream=stream)
     tuning = {k: v for k, v in tuned.items() if v}
     tuning["profile"] = 1
+    if args.pass_loop == "host":  # each depth-first pass launched by the host (profilers
+        tuning["graph"] = -1      # cannot see kernels inside conditional graph nodes)
 
     # counts first (untimed): they size the output lists
     res = wpm.enumerate_batch(specs, list_mode=False, tuning=tuning, stream=stream)
@@ -328,6 +330,7 @@ def run_ours(args, rank, world):
                    "l2": "not flushed: each step streams GBs (work ring, output lists) through "
                          "the 129 MB L2",
                    "tuning": {k: v for k, v in tuning.items() if k != "profile"},
+                   "pass_loop": args.pass_loop,
                    "tuning_from": "wpm_autotune on every 16th map of the batch"},
         "instances_per_s": inst_per_s,
         "nodes_per_step": nodes_step * world,
@@ -364,6 +367,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--plain-sample", type=int, default=256)
     ap.add_argument("--cpu-stride", type=int, default=64, help="oracle sample: every k-th instance")
+    ap.add_argument("--pass-loop", default="graph", choices=["graph", "host"],
+                    help="depth-first passes as one CUDA graph launch, or launched by the host")
     ap.add_argument("--table1", type=int, default=1,
                     help="time every IDCM orbit of n = 8..11 beside the paper's Table 1")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="serving: arrivals per s")
