@@ -11,6 +11,8 @@ path (candidate facets, ridges, search, per-instance sort) over the 4096 instanc
   e2e    the same metric through the C ABI with host buffers: the step includes copying
          the inputs in and every sorted mask list out to pinned host memory
 
+  plain_configs  the single-map workloads (Fano n = 3 and n = 5 maps, 16 seeds each, full
+         lists; the whole n = 11 map, count only), one plain call per map
   paper_table1  every IDCM orbit of n = 8..11 under the cap alone (the paper's Table 1
          workload), seconds per orbit beside the paper's times (other hardware, other
          algorithm: context only)
@@ -167,6 +169,34 @@ def run_serving(args):
 # on an Nvidia Quadro A5000 (n = 11: the authors' estimate, not a run).
 PAPER_TABLE1_SECONDS_PER_ORBIT = {8: 15 * 60.0, 9: 2 * 3600.0, 10: 12 * 86400.0,
                                   11: 3 * 365 * 86400.0}
+
+
+def run_plain_configs(stream):
+    """The single-map workloads, each map by one plain wpm_enumerate call (full sorted list,
+    except the n = 11 map: count only): the Fano map (n = 3) for 16 seeds, n = 5 dual maps
+    for 16 seeds, and the whole n = 11 map (all 15 nonzero rows of Z2^4, seed 0)."""
+    import torch
+    from paper_2301_00806_gb300 import instances as I, wpm
+    out = {}
+    cases = [("fano_n3", [I.fano_primal(s) for s in range(16)], True),
+             ("dual_n5", [I.single_dual(5, s) for s in range(16)], True),
+             ("full_n11", [I.full_dual_n11(0)], False)]
+    for name, insts, lists in cases:
+        i0 = insts[0]
+        wpm.enumerate(i0.kind, i0.n, i0.m, i0.cols, cap=wpm.CAP_UBT, list_mode=False)  # warm-up
+        torch.cuda.synchronize()
+        nodes = count = 0
+        t0 = time.perf_counter()
+        for i in insts:
+            r = wpm.enumerate(i.kind, i.n, i.m, i.cols, cap=wpm.CAP_UBT, list_mode=lists,
+                              capacity=1 << 16)
+            nodes += r.nodes
+            count += r.count
+        dt = time.perf_counter() - t0
+        out[name] = {"maps": len(insts), "wpms": count, "nodes": nodes, "seconds": dt,
+                     "nodes_per_s": nodes / dt, "maps_per_s": len(insts) / dt,
+                     "mode": "list" if lists else "count"}
+    return out
 
 
 def run_paper_table1(stream):
@@ -350,6 +380,7 @@ def run_ours(args, rank, world):
         "clocks": clocks,
     }
     if world == 1 and args.table1:
+        line["plain_configs"] = run_plain_configs(stream)
         line["paper_table1"] = run_paper_table1(stream)
     if world == 1 and args.serve_seconds > 0:
         line["serving"] = run_serving(args)
