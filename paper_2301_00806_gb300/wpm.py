@@ -360,10 +360,12 @@ class Engine:
         self._modes = {}
 
     def submit(self, kind, n, m, cols, cap=CAP_NONE, base_facet=False, forced_in=None,
-               forced_out=None, affine=None, n_facets=0, list_mode=False, capacity=0) -> int:
+               forced_out=None, affine=None, n_facets=0, list_mode=False, capacity=0,
+               post_filter=0) -> int:
         keep = _Keep()
         cc = keep.add(np.asarray(cols, dtype=np.uint32))
-        cond = _conditions(cap, base_facet, n_facets, forced_in, forced_out, affine, keep)
+        cond = _conditions(cap, base_facet, n_facets, forced_in, forced_out, affine, keep,
+                           post_filter)
         inst = Instance()
         inst.kind = _KIND[kind]
         inst.n = n

@@ -85,3 +85,13 @@ def test_engine_capacity_and_limits(W):
     assert got[small].status == W.ERR_CAPACITY and got[small].count > 10
     assert got[big].status == W.ERR_LIMIT
     E.close()
+
+
+def test_engine_refuses_post_filters(W):
+    E = W.Engine(max_n=5, max_jobs=2, budget=256, memory_bytes=1 << 26)
+    inst = I.single_dual(5, 2)
+    with pytest.raises(W.WpmError) as e:
+        E.submit("dual", 5, 9, inst.cols, cap=-2, list_mode=True, capacity=1 << 12,
+                 post_filter=W.POST_SEED)
+    assert e.value.code == W.ERR_INPUT
+    E.close()
