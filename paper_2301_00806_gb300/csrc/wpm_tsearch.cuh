@@ -13,12 +13,16 @@
 // returned to the work ring carries only its untried children: a ridge level's tried parents
 // join Out, a seed level's floor moves past its tried facets.
 //
-// A pass ends for a search when it has spent its node budget or when enough searches of the
-// pass have found the ring empty. It then gives its shallowest open levels to the ring (the
-// largest untried subtrees; how many depends on how short of items the ring is) and parks the
-// rest of its work in its own park record (node state, top entry, depth; the stack stays in
-// place), to resume it at the start of the next pass. Giving and parking never change which
-// nodes are searched, so counts do not depend on pass boundaries.
+// Work moves between searches inside a pass: while searches wait for items and the ring
+// holds fewer items than are waiting, a busy search gives its shallowest open levels (the
+// largest untried subtrees) to the ring and goes on with the rest; items written during the
+// pass carry a ready flag, so a waiting search takes them at once. A pass ends when every
+// search waits or has left and no item is left, or, for a search, when its node budget or
+// time is spent or the ring has no room: it then gives a few shallowest levels while the ring
+// is short of items and parks the rest of its work in its own park record (node state, top
+// entry, depth; the stack stays in place), to resume it at the start of the next pass.
+// Giving and parking never change which nodes are searched, so counts do not depend on where
+// work is split.
 //
 // Per-thread state lives in shared memory, word w of thread t at [w * TPB + t], so every
 // dynamically indexed access of a warp hits 32 distinct banks:
