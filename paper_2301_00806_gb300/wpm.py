@@ -333,7 +333,8 @@ def enumerate_batch(specs: List[BatchSpec], list_mode=True, capacities=None, tun
         masks = None
         if list_mode and bufs[i] is not None and o.status == OK:
             w = int(o.words_per_mask)
-            masks = bufs[i][: int(o.count) * w].reshape(int(o.count), w).copy()
+            # a view of the buffer the library filled (no second copy of the list)
+            masks = bufs[i][: int(o.count) * w].reshape(int(o.count), w)
         res.append(_result(o, masks))
     return res
 
