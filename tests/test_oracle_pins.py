@@ -319,7 +319,7 @@ def test_n11_subtree_golden_file_reproduces():
 # Proposition 3.1
 # ---------------------------------------------------------------------------------------
 
-TABLE2_LINE13 = {2: 22, 3: 578, 4: 13679, 5: 47012}  # Table 2, |K(n,4)| at line 13
+TABLE2_LINE13 = {2: 22, 3: 578, 4: 13679, 5: 47012, 6: 204714}  # Table 2, line 13
 
 
 @pytest.mark.parametrize("n", sorted(TABLE2_LINE13))
