@@ -280,7 +280,7 @@ typedef struct wpm_engine wpm_engine;
 typedef struct {
     int64_t memory_bytes;   /* device memory for job outputs; 0 = 8 GiB                   */
     int32_t max_jobs;       /* concurrent jobs (slots); 0 = 1024                          */
-    int32_t budget;         /* most search nodes per search per step; 0 = 8192            */
+    int32_t budget;         /* most search nodes per search per step; 0 = 16384           */
     int32_t max_n;          /* largest n admitted (sets the kernel size class and the
                                search depth, the upper-bound cap of n); 0 = 11             */
     int32_t reserved;

@@ -396,7 +396,7 @@ int wpm_engine_create(const wpm_engine_config *cfg, void *cuda_stream, wpm_engin
   const int64_t mem = cfg && cfg->memory_bytes > 0 ? cfg->memory_bytes : (8ll << 30);
   e->max_jobs = cfg && cfg->max_jobs > 0 ? cfg->max_jobs : 1024;
   e->max_n = cfg && cfg->max_n > 0 ? std::min(cfg->max_n, 12) : 11;
-  e->budget = cfg && cfg->budget > 0 ? cfg->budget : 8192;
+  e->budget = cfg && cfg->budget > 0 ? cfg->budget : 16384;
   auto bail = [&](int code) {
     wpm_engine_destroy(e);
     return code;

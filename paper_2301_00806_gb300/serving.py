@@ -53,7 +53,7 @@ class ServeStats:
 
 
 def serve(jobs, list_mode: bool = True, max_n: int = 9, max_jobs: int = 1024,
-          budget: int = 8192, memory_bytes: int = 16 << 30, capacity: Dict[int, int] = None,
+          budget: int = 16384, memory_bytes: int = 16 << 30, capacity: Dict[int, int] = None,
           stream=None, deadline_s: float = 0.0, log=None) -> ServeStats:
     """Serve `jobs` (instances with extra['t_arrival'] in seconds) in real time. With
     deadline_s > 0 the loop gives up after that many seconds (unfinished jobs are left out of
