@@ -30,12 +30,13 @@ def _drain(E, want):
     return got
 
 
-@pytest.mark.parametrize("max_n", [6, 9])
-def test_jobs_alone_and_in_the_mix_agree(W, max_n):
+@pytest.mark.parametrize("max_n,budget", [(6, 512), (9, 512), (9, 0)],
+                         ids=["n6", "n9", "n9_default_budget"])
+def test_jobs_alone_and_in_the_mix_agree(W, max_n, budget):
     jobs = I.poisson_jobs(rate=200.0, duration=0.2, n_lo=5, n_hi=max_n, seed=3)
     assert len(jobs) >= 20
     alone = [W.enumerate("dual", j.n, j.m, j.cols, cap=-2, capacity=1 << 17) for j in jobs]
-    E = W.Engine(max_n=max_n, max_jobs=16, budget=512, memory_bytes=1 << 30)
+    E = W.Engine(max_n=max_n, max_jobs=16, budget=budget, memory_bytes=1 << 30)
     ids = []
     got = {}
     # submit in arrival order, stepping between arrivals so that jobs join a running mix
