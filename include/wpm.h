@@ -244,10 +244,11 @@ int wpm_enumerate_batch(const wpm_instance *inst, int count, wpm_output *outs, i
  * hand-overs) on a sample of the batch, every k-th instance for about `sample` instances
  * (0: 256), in counting mode, and writes the fastest to *best. Counts do not depend on the
  * tuning, so the candidates differ only in time. The choice is also kept, for the rest of
- * the process, under the batch's signature (the smallest and largest n, and whether any map
- * is primal): wpm_enumerate_batch with tuning == NULL on a batch of the same signature uses
- * it. best_ms (optional) receives the winner's time on the sample, in milliseconds.
- * Errors as wpm_enumerate_batch's; instances that fail their own checks are left out.
+ * the process, under the batch's signature (the smallest and largest n, whether any map is
+ * primal, and the number of maps rounded down to a power of two): wpm_enumerate_batch with
+ * tuning == NULL on a batch of the same signature uses it. best_ms (optional) receives the
+ * winner's time on the sample, in milliseconds. Errors as wpm_enumerate_batch's; instances
+ * that fail their own checks are left out.
  */
 int wpm_autotune(const wpm_instance *inst, int count, int sample, wpm_tuning *best,
                  double *best_ms, void *cuda_stream);

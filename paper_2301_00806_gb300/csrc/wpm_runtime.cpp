@@ -986,7 +986,8 @@ static int single(HostInst &h, wpm_output *out, int mode) {
 using namespace wpm;
 
 // ---- autotuner ---------------------------------------------------------------------------
-// Signature of a batch: smallest and largest n, and whether any map is primal.
+// Signature of a batch: smallest and largest n, whether any map is primal, and the size
+// of the batch to a power of two (few maps and many maps want different searches).
 static uint64_t batch_signature(const wpm_instance *inst, int count) {
   int lo = 99, hi = 0, primal = 0;
   for (int i = 0; i < count; i++) {
@@ -994,7 +995,10 @@ static uint64_t batch_signature(const wpm_instance *inst, int count) {
     hi = std::max(hi, (int)inst[i].n);
     primal |= inst[i].kind == WPM_LAMBDA_PRIMAL;
   }
-  return ((uint64_t)lo << 16) | ((uint64_t)hi << 1) | (uint64_t)primal;
+  int size_log2 = 0;
+  while ((1 << (size_log2 + 1)) <= count && size_log2 < 30) size_log2++;
+  return ((uint64_t)size_log2 << 24) | ((uint64_t)lo << 16) | ((uint64_t)hi << 1) |
+         (uint64_t)primal;
 }
 
 static std::map<uint64_t, wpm_tuning> g_tuned;  // guarded by g_mu
