@@ -926,3 +926,142 @@ long orc_filter_pic_seed(int n, int m, int M, const uint16_t *facets, const uint
     free(kf);
     return kept;
 }
+
+/* ---------------------------------------------------------------------------------- */
+/* Algorithm 4.4, line 14: one representative per isomorphism class. Two complexes are  */
+/* isomorphic when a relabeling of the vertices maps the facets of one onto the facets  */
+/* of the other. The canonical form of K is the smallest sorted list of relabeled facet */
+/* masks over the leaves of a search that (1) colors the vertices by an invariant,      */
+/* refined until stable (a vertex's new color: its color, then the sorted colors of the */
+/* other vertices of each facet through it, those lists sorted), and (2) while some     */
+/* color is shared, tries each vertex of the first shared color as a color of its own.  */
+/* Every step uses invariants only, so isomorphic complexes get the same form.          */
+/* ---------------------------------------------------------------------------------- */
+
+typedef struct {
+    int m, n, k;
+    uint16_t f[512];
+    uint16_t best[512];
+    int have_best;
+} canon_t;
+
+/* one vertex's signature: its color, then the facets through it, each as the sorted colors
+   of its other vertices, the facets sorted; written into sig (ints), returns the length */
+static int vertex_signature(const canon_t *C, const int *col, int v, int *sig)
+{
+    int len = 0, nf = 0;
+    int rows[512][16];
+    sig[len++] = col[v];
+    for (int i = 0; i < C->k; i++) {
+        if (!((C->f[i] >> v) & 1u)) continue;
+        int r = 0;
+        for (int u = 0; u < C->m; u++)
+            if (u != v && ((C->f[i] >> u) & 1u)) rows[nf][r++] = col[u];
+        for (int a = 1; a < r; a++)              /* insertion sort of the row */
+            for (int b = a; b > 0 && rows[nf][b - 1] > rows[nf][b]; b--) {
+                int t = rows[nf][b]; rows[nf][b] = rows[nf][b - 1]; rows[nf][b - 1] = t;
+            }
+        for (int j = r; j < 16; j++) rows[nf][j] = -1;
+        nf++;
+    }
+    for (int a = 1; a < nf; a++)                 /* sort the rows lexicographically */
+        for (int b = a; b > 0 && memcmp(rows[b - 1], rows[b], sizeof(rows[0])) > 0; b--) {
+            int t[16];
+            memcpy(t, rows[b], sizeof(t)); memcpy(rows[b], rows[b - 1], sizeof(t));
+            memcpy(rows[b - 1], t, sizeof(t));
+        }
+    sig[len++] = nf;
+    for (int a = 0; a < nf; a++)
+        for (int j = 0; j < 16; j++) sig[len++] = rows[a][j];
+    return len;
+}
+
+static int cmp_sig(const int *a, int la, const int *b, int lb)
+{
+    int l = la < lb ? la : lb;
+    for (int i = 0; i < l; i++)
+        if (a[i] != b[i]) return a[i] < b[i] ? -1 : 1;
+    return la == lb ? 0 : (la < lb ? -1 : 1);
+}
+
+/* refine col (ranks 0..) until the number of colors stops growing */
+static void refine(const canon_t *C, int *col)
+{
+    static int sig[16][2 + 512 * 16];
+    int len[16];
+    for (;;) {
+        int before = 0;
+        for (int v = 0; v < C->m; v++) if (col[v] + 1 > before) before = col[v] + 1;
+        for (int v = 0; v < C->m; v++) len[v] = vertex_signature(C, col, v, sig[v]);
+        int idx[16], newcol[16];                /* vertices sorted by signature */
+        for (int v = 0; v < C->m; v++) idx[v] = v;
+        for (int a = 1; a < C->m; a++)
+            for (int b = a; b > 0 && cmp_sig(sig[idx[b - 1]], len[idx[b - 1]],
+                                             sig[idx[b]], len[idx[b]]) > 0; b--) {
+                int t = idx[b]; idx[b] = idx[b - 1]; idx[b - 1] = t;
+            }
+        int rank = 0;                           /* equal signatures share a rank */
+        for (int a = 0; a < C->m; a++) {
+            if (a > 0 && cmp_sig(sig[idx[a - 1]], len[idx[a - 1]], sig[idx[a]], len[idx[a]]) != 0)
+                rank++;
+            newcol[idx[a]] = rank;
+        }
+        int after = 0;
+        for (int v = 0; v < C->m; v++) if (newcol[v] + 1 > after) after = newcol[v] + 1;
+        memcpy(col, newcol, sizeof(int) * C->m);
+        if (after == before) return;
+    }
+}
+
+static int cmp_u16(const void *a, const void *b)
+{
+    uint16_t x = *(const uint16_t *)a, y = *(const uint16_t *)b;
+    return (x > y) - (x < y);
+}
+
+static void canon_search(canon_t *C, int *col)
+{
+    refine(C, col);
+    int count[16] = {0};
+    for (int v = 0; v < C->m; v++) count[col[v]]++;
+    int target = -1;
+    for (int c = 0; c < C->m; c++) if (count[c] > 1) { target = c; break; }
+    if (target < 0) {                           /* discrete: vertex v gets label col[v] */
+        uint16_t g[512];
+        for (int i = 0; i < C->k; i++) {
+            uint16_t x = 0;
+            for (int v = 0; v < C->m; v++) if ((C->f[i] >> v) & 1u) x |= (uint16_t)(1u << col[v]);
+            g[i] = x;
+        }
+        qsort(g, (size_t)C->k, sizeof(uint16_t), cmp_u16);
+        int better = !C->have_best;
+        for (int i = 0; i < C->k && !better; i++) {
+            if (g[i] != C->best[i]) { better = g[i] < C->best[i]; break; }
+        }
+        if (better) { memcpy(C->best, g, sizeof(uint16_t) * (size_t)C->k); C->have_best = 1; }
+        return;
+    }
+    for (int v = 0; v < C->m; v++) {
+        if (col[v] != target) continue;
+        int c2[16];                             /* v keeps the color, its cell mates move up */
+        for (int u = 0; u < C->m; u++)
+            c2[u] = col[u] > target ? col[u] + 1 : (col[u] == target && u != v ? target + 1 : col[u]);
+        canon_search(C, c2);
+    }
+}
+
+/* Canonical form of K (k facets as vertex masks on [m], m <= 16, k <= 512): the sorted
+   relabeled facet masks in out[0..k). Returns 0, or -1 on bad input. */
+int orc_canonical_form(int m, int k, const uint16_t *facets, uint16_t *out)
+{
+    if (m < 1 || m > 16 || k < 0 || k > 512) return -1;
+    canon_t *C = (canon_t *)calloc(1, sizeof(canon_t));
+    if (!C) return -1;
+    C->m = m; C->k = k;
+    memcpy(C->f, facets, sizeof(uint16_t) * (size_t)k);
+    int col[16] = {0};
+    canon_search(C, col);
+    memcpy(out, C->best, sizeof(uint16_t) * (size_t)k);
+    free(C);
+    return 0;
+}

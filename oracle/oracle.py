@@ -73,6 +73,7 @@ def lib():
             L.orc_filter_pic_seed.argtypes = [C.c_int, C.c_int, C.c_int, u16p, u64p, C.c_long,
                                               C.c_int, C.POINTER(C.c_uint8)]
             L.orc_filter_pic_seed.restype = C.c_long
+            L.orc_canonical_form.argtypes = [C.c_int, C.c_int, u16p, u16p]
             L.orc_n2_cycle_sets.argtypes = [C.c_int, u16p, C.c_int]
             L.orc_n2_cycle_sets.restype = C.c_long
             L.orc_n2_cycle_count.argtypes = [C.c_int, u16p]
@@ -260,3 +261,19 @@ def filter_pic_seed(n, m, facets, masks):
     _check(lib().orc_filter_pic_seed(n, m, f.size, _p(f, C.c_uint16), _p(mk, C.c_uint64),
                                      count, W, _p(keep, C.c_uint8)), "filter_pic_seed")
     return keep[:count]
+
+
+def canonical_form(m, facet_masks) -> tuple:
+    """Algorithm 4.4 line 14: a canonical form of K (facets as vertex masks on [m]) under
+    vertex relabeling; isomorphic complexes, and only they, have equal forms."""
+    kf = np.ascontiguousarray(facet_masks, dtype=np.uint16)
+    out = np.zeros(max(kf.size, 1), dtype=np.uint16)
+    _check(lib().orc_canonical_form(m, kf.size, _p(kf, C.c_uint16), _p(out, C.c_uint16)),
+           "canonical_form")
+    return tuple(int(x) for x in out[:kf.size])
+
+
+def masks_to_facets(facets, mask_row):
+    """Vertex masks of the facets selected by one output mask row."""
+    M = len(facets)
+    return [int(facets[j]) for j in range(M) if (int(mask_row[j // 64]) >> (j % 64)) & 1]

@@ -386,3 +386,47 @@ def test_suspension_keeps_seedness():
 
 def test_unused_vertex_fails_pic():
     assert O.pic_seed(2, 7, _hexagon()) is False
+
+
+# ---------------------------------------------------------------------------------------
+# Algorithm 4.4 line 14: one representative per isomorphism class (canonical forms)
+# ---------------------------------------------------------------------------------------
+
+TABLE2_LINE15 = {2: 2, 3: 5, 4: 49, 5: 256}  # Table 2, |K°(n,4)| at line 15
+
+
+def _line13_complexes(n):
+    out = []
+    for rows in I.idcm_orbit_reps(n):
+        f = O.candidate_facets("dual", n, n + 4, rows)
+        _, _, _, masks = O.enumerate_dfs(n, n + 4, f, cap=-2, base_facet=True,
+                                         capacity=1 << 17)
+        keep = O.filter_pic_seed(n, n + 4, f, masks)
+        out += [O.masks_to_facets(f, row) for row, k in zip(masks, keep) if k]
+    return out
+
+
+@pytest.mark.parametrize("n", sorted(TABLE2_LINE15))
+def test_table2_line15_isomorphism_classes(n):
+    forms = {O.canonical_form(n + 4, K) for K in _line13_complexes(n)}
+    assert len(forms) == TABLE2_LINE15[n]
+
+
+def _relabel(K, perm):
+    return [sum(1 << perm[v] for v in range(16) if (F >> v) & 1) for F in K]
+
+
+def test_canonical_form_is_invariant_under_relabeling():
+    rng = np.random.default_rng(5)
+    cx = _line13_complexes(4)
+    for K in [cx[i] for i in rng.choice(len(cx), size=40, replace=False)]:
+        base = O.canonical_form(8, K)
+        for _ in range(3):
+            perm = list(rng.permutation(8))
+            assert O.canonical_form(8, _relabel(K, perm)) == base
+
+
+def test_canonical_form_separates_non_isomorphic():
+    hexagon = [_mask((i, (i + 1) % 6)) for i in range(6)]
+    triangles = [_mask(e) for e in ((0, 1), (1, 2), (0, 2), (3, 4), (4, 5), (3, 5))]
+    assert O.canonical_form(6, hexagon) != O.canonical_form(6, triangles)
