@@ -254,6 +254,19 @@ int wpm_autotune(const wpm_instance *inst, int count, int sample, wpm_tuning *be
                  double *best_ms, void *cuda_stream);
 
 /*
+ * Isomorphism classes (Algorithm 4.4, line 14: one representative per class). Complex c,
+ * for c = 0..count-1, has the facets facets[offsets[c] .. offsets[c+1]) (vertex masks on
+ * [m], m <= 16; host pointers, offsets has count + 1 entries). Two complexes are in one class
+ * when a relabeling of the vertices maps the facets of one onto the facets of the other.
+ * class_of[c] receives the class of complex c, classes numbered 0.. in order of first
+ * appearance; returns the number of classes, or a negative error code. Computed on the host
+ * (several threads): a canonical form per complex, by colour refinement and
+ * individualization. Runs without a GPU.
+ */
+long wpm_iso_classes(int m, int count, const uint64_t *offsets, const uint16_t *facets,
+                     int32_t *class_of);
+
+/*
  * wpm_candidate_facets with no allocation (the paper has no counterpart: this serves callers
  * that must not allocate, e.g. a service that reserved its device memory at start-up, a host
  * framework whose allocator owns the device, or code running while a stream is captured into

@@ -119,6 +119,8 @@ def lib():
             L.wpm_last_error.restype = C.c_char_p
             L.wpm_autotune.argtypes = [C.POINTER(Instance), C.c_int, C.c_int, C.POINTER(Tuning),
                                        C.POINTER(C.c_double), C.c_void_p]
+            L.wpm_iso_classes.argtypes = [C.c_int, C.c_int, u64p, u16p, C.POINTER(C.c_int32)]
+            L.wpm_iso_classes.restype = C.c_long
             L.wpm_last_run_stats.argtypes = [C.POINTER(RunStats)]
             L.wpm_release_workspace.argtypes = []
             L.wpm_engine_create.argtypes = [C.POINTER(EngineConfig), C.c_void_p, C.POINTER(C.c_void_p)]
@@ -468,3 +470,31 @@ def last_run_stats() -> dict:
 
 def release_workspace() -> None:
     lib().wpm_release_workspace()
+
+
+def complexes_from_masks(facets, masks):
+    """(vertex masks of the selected facets, concatenated; offsets) of output masks (count,
+    W) of a map whose candidate facets (vertex masks, lexicographic order) are `facets`."""
+    f = np.asarray(facets, dtype=np.uint16)
+    mk = np.ascontiguousarray(masks, dtype=np.uint64)
+    if mk.size == 0:
+        return np.zeros(0, dtype=np.uint16), np.zeros(1, dtype=np.uint64)
+    bits = np.unpackbits(mk.view(np.uint8).reshape(mk.shape[0], -1), axis=1,
+                         bitorder="little")[:, : f.size].astype(bool)
+    flat = np.broadcast_to(f, bits.shape)[bits]
+    offsets = np.concatenate([[0], np.cumsum(bits.sum(axis=1))]).astype(np.uint64)
+    return np.ascontiguousarray(flat, dtype=np.uint16), offsets
+
+
+def iso_classes(m: int, flat, offsets):
+    """wpm_iso_classes: (class of each complex, number of classes) for complexes given as
+    concatenated facet vertex masks with offsets (see complexes_from_masks)."""
+    fl = np.ascontiguousarray(flat, dtype=np.uint16)
+    off = np.ascontiguousarray(offsets, dtype=np.uint64)
+    count = off.size - 1
+    cls = np.zeros(max(count, 1), dtype=np.int32)
+    n = lib().wpm_iso_classes(m, count, _p(off, C.c_uint64), _p(fl, C.c_uint16),
+                              _p(cls, C.c_int32))
+    if n < 0:
+        raise _err(int(n))
+    return cls[:count], int(n)

@@ -79,3 +79,26 @@ def test_post_filter_errors(W):
     with pytest.raises(W.WpmError) as e:
         W.enumerate_batch([bad], list_mode=True, capacities=[1 << 12])
     assert e.value.code == W.ERR_INPUT
+
+
+TABLE2_LINE15 = {2: 2, 3: 5, 4: 49, 5: 256, 6: 1791, 7: 2194, 8: 1401, 9: 381, 10: 56}
+
+
+@pytest.mark.parametrize("n", sorted(TABLE2_LINE15))
+def test_table2_line15(W, n):
+    """Algorithm 4.4 lines 1-15: GPU enumeration and post-filters over one map per IDCM
+    orbit, then the library's isomorphism classes (host) across all of them."""
+    reps = I.idcm_orbit_reps(n)
+    specs = [W.BatchSpec("dual", n, n + 4, r, cap=-2, base_facet=True) for r in reps]
+    counts = [r.count for r in W.enumerate_batch(specs, list_mode=False)]
+    fspecs = [W.BatchSpec("dual", n, n + 4, r, cap=-2, base_facet=True, post_filter=BOTH)
+              for r in reps]
+    res = W.enumerate_batch(fspecs, list_mode=True, capacities=[max(1, c) for c in counts])
+    flats, offs = [], [0]
+    for r, rows in zip(res, reps):
+        f = W.candidate_facets("dual", n, n + 4, rows)
+        fl, of = W.complexes_from_masks(f, r.masks)
+        flats.append(fl)
+        offs += list(offs[-1] + of[1:].astype(np.int64))
+    _, classes = W.iso_classes(n + 4, np.concatenate(flats), np.asarray(offs, dtype=np.uint64))
+    assert classes == TABLE2_LINE15[n]

@@ -1,0 +1,57 @@
+"""Isomorphism classes (Algorithm 4.4, line 14) computed by the library's host routine
+wpm_iso_classes, which needs no GPU: the same partition as the oracle's canonical forms on
+the line-13 complexes of n = 2..5 (built by the oracle), hence Table 2's line-15 counts."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2301_00806_gb300 import instances as I, wpm
+
+TABLE2_LINE15 = {2: 2, 3: 5, 4: 49, 5: 256}
+
+
+def _complexes(n):
+    flats, offs = [], [0]
+    for rows in I.idcm_orbit_reps(n):
+        f = O.candidate_facets("dual", n, n + 4, rows)
+        _, _, _, masks = O.enumerate_dfs(n, n + 4, f, cap=-2, base_facet=True,
+                                         capacity=1 << 17)
+        keep = O.filter_pic_seed(n, n + 4, f, masks).astype(bool)
+        fl, of = wpm.complexes_from_masks(f, masks[keep])
+        flats.append(fl)
+        offs += list(offs[-1] + of[1:].astype(np.int64))
+    return np.concatenate(flats), np.asarray(offs, dtype=np.uint64)
+
+
+@pytest.mark.parametrize("n", sorted(TABLE2_LINE15))
+def test_iso_classes_match_the_oracle(n):
+    flat, off = _complexes(n)
+    cls, count = wpm.iso_classes(n + 4, flat, off)
+    assert count == TABLE2_LINE15[n]
+    forms, want = {}, []
+    for c in range(off.size - 1):
+        f = O.canonical_form(n + 4, flat[off[c]:off[c + 1]])
+        want.append(forms.setdefault(f, len(forms)))
+    assert np.array_equal(cls, np.asarray(want, dtype=np.int32))
+
+
+def test_iso_classes_of_relabeled_copies():
+    flat, off = _complexes(4)
+    rng = np.random.default_rng(11)
+    pick = rng.choice(off.size - 1, size=30, replace=False)
+    fl2, off2 = [], [0]
+    for c in pick:  # each picked complex, then a randomly relabeled copy of it
+        K = flat[off[c]:off[c + 1]].astype(int)
+        perm = rng.permutation(8)
+        R = np.array([sum(1 << int(perm[v]) for v in range(8) if (F >> v) & 1) for F in K])
+        for X in (K, R):
+            fl2.append(X)
+            off2.append(off2[-1] + len(X))
+    cls, _ = wpm.iso_classes(8, np.concatenate(fl2).astype(np.uint16),
+                             np.asarray(off2, dtype=np.uint64))
+    assert np.array_equal(cls[0::2], cls[1::2])
+
+
+def test_iso_classes_input_errors():
+    with pytest.raises(wpm.WpmError):
+        wpm.iso_classes(6, np.array([1 << 7], dtype=np.uint16), np.array([0, 1], dtype=np.uint64))
