@@ -1065,3 +1065,105 @@ int orc_canonical_form(int m, int k, const uint16_t *facets, uint16_t *out)
     free(C);
     return 0;
 }
+
+/* ---------------------------------------------------------------------------------- */
+/* Algorithm 4.4, line 16: PL sphereness by the criterion of Lemma 3.3 (PL sphereness): */
+/* a WPM of Picard number <= 7 is a PL sphere exactly when the link of every face,      */
+/* the empty face included, is a Z2-homology sphere: its reduced Z2-homology is Z2 in   */
+/* its top dimension and zero below. Faces and links are read off a bitmap of all 2^m   */
+/* vertex subsets; reduced Betti numbers come from GF(2) ranks of boundary matrices.    */
+/* ---------------------------------------------------------------------------------- */
+
+/* GF(2) rank of nrows rows of W words (the rows are overwritten) */
+static int gf2_rank_rows(uint64_t *rows, int nrows, int W)
+{
+    int rank = 0;
+    for (int col = 0; col < W * 64 && rank < nrows; col++) {
+        int w = col / 64;
+        uint64_t bit = 1ull << (col % 64);
+        int piv = -1;
+        for (int r = rank; r < nrows; r++)
+            if (rows[(size_t)r * W + w] & bit) { piv = r; break; }
+        if (piv < 0) continue;
+        if (piv != rank)
+            for (int x = 0; x < W; x++) {
+                uint64_t t = rows[(size_t)piv * W + x];
+                rows[(size_t)piv * W + x] = rows[(size_t)rank * W + x];
+                rows[(size_t)rank * W + x] = t;
+            }
+        for (int r = 0; r < nrows; r++)
+            if (r != rank && (rows[(size_t)r * W + w] & bit))
+                for (int x = 0; x < W; x++) rows[(size_t)r * W + x] ^= rows[(size_t)rank * W + x];
+        rank++;
+    }
+    return rank;
+}
+
+/* 1 when the link of sigma (a face; face[] the face bitmap of K over [m]) is a Z2-homology
+   sphere of dimension d = dim K - |sigma| */
+static int link_is_z2_sphere(const char *face, int m, uint32_t sigma, int d)
+{
+    uint32_t nsub = 1u << m;
+    uint32_t rest = (nsub - 1u) & ~sigma;
+    /* link faces by size: tau subset of rest with tau | sigma a face */
+    int *idx = (int *)malloc(sizeof(int) * nsub);
+    int cnt[18] = {0};
+    uint32_t *list[18];
+    for (int s = 0; s <= d + 1 && s < 18; s++) list[s] = (uint32_t *)malloc(sizeof(uint32_t) * nsub);
+    for (uint32_t t = rest;; t = (t - 1) & rest) {
+        if (face[t | sigma]) {
+            int s = __builtin_popcount(t);
+            if (s <= d + 1) { idx[t] = cnt[s]; list[s][cnt[s]++] = t; }
+        }
+        if (t == 0) break;
+    }
+    /* rank of the boundary from size s faces to size s-1 faces, s = 1..d+1 */
+    int rk[19] = {0};
+    for (int s = 1; s <= d + 1; s++) {
+        int rows = cnt[s], cols = cnt[s - 1];
+        if (!rows || !cols) continue;
+        int W = (cols + 63) / 64;
+        uint64_t *mat = (uint64_t *)calloc((size_t)rows * W, sizeof(uint64_t));
+        for (int r = 0; r < rows; r++) {
+            uint32_t t = list[s][r];
+            for (int v = 0; v < m; v++)
+                if ((t >> v) & 1u) {
+                    int c = idx[t & ~(1u << v)];
+                    mat[(size_t)r * W + c / 64] ^= 1ull << (c % 64);
+                }
+        }
+        rk[s] = gf2_rank_rows(mat, rows, W);
+        free(mat);
+    }
+    /* reduced Betti number in dimension i (faces of size i + 1): cnt - rank out - rank in */
+    int ok = 1;
+    for (int s = 0; s <= d + 1 && ok; s++) {
+        int betti = cnt[s] - rk[s] - (s + 1 <= d + 1 ? rk[s + 1] : 0);
+        int want = (s == d + 1) ? 1 : 0;
+        if (betti != want) ok = 0;
+    }
+    for (int s = 0; s <= d + 1 && s < 18; s++) free(list[s]);
+    free(idx);
+    return ok;
+}
+
+/* 1 when K (k facets, vertex masks on [m], every facet of n vertices) satisfies Lemma 3.3's
+   criterion; 0 otherwise; -1 on bad input. */
+int orc_pl_sphere(int n, int m, int k, const uint16_t *kf)
+{
+    if (m < 1 || m > 15 || n < 1 || k < 0) return -1;
+    uint32_t nsub = 1u << m;
+    char *face = (char *)calloc(nsub, 1);
+    if (!face) return -1;
+    for (uint32_t S = 0; S < nsub; S++)
+        for (int i = 0; i < k; i++)
+            if ((S & ~(uint32_t)kf[i]) == 0) { face[S] = 1; break; }
+    int ok = 1;
+    for (uint32_t S = 0; S < nsub && ok; S++) {
+        if (!face[S]) continue;
+        int d = (n - 1) - __builtin_popcount(S);  /* dimension of the link of S */
+        if (!link_is_z2_sphere(face, m, S, d)) ok = 0;
+    }
+    free(face);
+    return ok;
+}

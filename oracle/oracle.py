@@ -74,6 +74,7 @@ def lib():
                                               C.c_int, C.POINTER(C.c_uint8)]
             L.orc_filter_pic_seed.restype = C.c_long
             L.orc_canonical_form.argtypes = [C.c_int, C.c_int, u16p, u16p]
+            L.orc_pl_sphere.argtypes = [C.c_int, C.c_int, C.c_int, u16p]
             L.orc_n2_cycle_sets.argtypes = [C.c_int, u16p, C.c_int]
             L.orc_n2_cycle_sets.restype = C.c_long
             L.orc_n2_cycle_count.argtypes = [C.c_int, u16p]
@@ -277,3 +278,10 @@ def masks_to_facets(facets, mask_row):
     """Vertex masks of the facets selected by one output mask row."""
     M = len(facets)
     return [int(facets[j]) for j in range(M) if (int(mask_row[j // 64]) >> (j % 64)) & 1]
+
+
+def pl_sphere(n, m, facet_masks) -> bool:
+    """Algorithm 4.4 line 16 by Lemma 3.3: the link of every face of K (the empty face
+    included) is a Z2-homology sphere."""
+    kf = np.ascontiguousarray(facet_masks, dtype=np.uint16)
+    return bool(_check(lib().orc_pl_sphere(n, m, kf.size, _p(kf, C.c_uint16)), "pl_sphere"))

@@ -406,10 +406,46 @@ def _line13_complexes(n):
     return out
 
 
+TABLE2_LINE19 = {2: 1, 3: 4, 4: 20, 5: 142}  # Table 2, |K°(n,4)| at line 19
+
+
+@pytest.fixture(scope="module")
+def line15_representatives():
+    """For n = 2..5: one line-13 complex per canonical form."""
+    reps = {}
+    for n in sorted(TABLE2_LINE15):
+        forms = {}
+        for K in _line13_complexes(n):
+            forms.setdefault(O.canonical_form(n + 4, K), K)
+        reps[n] = list(forms.values())
+    return reps
+
+
 @pytest.mark.parametrize("n", sorted(TABLE2_LINE15))
-def test_table2_line15_isomorphism_classes(n):
-    forms = {O.canonical_form(n + 4, K) for K in _line13_complexes(n)}
-    assert len(forms) == TABLE2_LINE15[n]
+def test_table2_line15_isomorphism_classes(n, line15_representatives):
+    assert len(line15_representatives[n]) == TABLE2_LINE15[n]
+
+
+@pytest.mark.parametrize("n", sorted(TABLE2_LINE19))
+def test_table2_line19_pl_spheres(n, line15_representatives):
+    got = sum(O.pl_sphere(n, n + 4, K) for K in line15_representatives[n])
+    assert got == TABLE2_LINE19[n]
+
+
+def test_pl_sphere_closed_cases():
+    import itertools
+    octahedron = [_mask((a, b, c)) for a in (0, 1) for b in (2, 3) for c in (4, 5)]
+    assert O.pl_sphere(3, 6, octahedron) is True
+    for n in range(2, 7):  # the boundary of a simplex
+        facets = [_mask(c) for c in itertools.combinations(range(n + 1), n)]
+        assert O.pl_sphere(n, n + 1, facets) is True
+    # the 6-vertex real projective plane: every edge in two triangles, H_1(RP^2; Z2) = Z2
+    rp2 = [_mask(t) for t in ((0, 1, 2), (0, 2, 3), (0, 3, 4), (0, 4, 5), (0, 5, 1),
+                              (1, 2, 4), (1, 3, 4), (1, 3, 5), (2, 3, 5), (2, 4, 5))]
+    assert O.pl_sphere(3, 6, rp2) is False
+    tri = [_mask(e) for e in ((0, 1), (1, 2), (0, 2), (3, 4), (4, 5), (3, 5))]
+    assert O.pl_sphere(2, 6, tri) is False                     # two circles
+    assert O.pl_sphere(3, 8, _suspension(tri, 6)) is False     # suspension of two circles
 
 
 def _relabel(K, perm):
