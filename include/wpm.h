@@ -267,6 +267,18 @@ long wpm_iso_classes(int m, int count, const uint64_t *offsets, const uint16_t *
                      int32_t *class_of);
 
 /*
+ * PL sphereness (Algorithm 4.4, line 16) by the criterion of Lemma 3.3: a weak
+ * pseudo-manifold of Picard number at most 7 is a PL sphere exactly when the link of every
+ * face, the empty face included, is a Z2-homology sphere. Complexes as in wpm_iso_classes
+ * (every facet an n-subset of [m], m <= 15); is_sphere[c] receives 1 or 0; returns the number
+ * of spheres, or a negative error code. Computed on the host (several threads): faces from a
+ * bitmap of all vertex subsets, reduced Z2-Betti numbers of every link from GF(2) ranks of its
+ * boundary maps. Runs without a GPU.
+ */
+long wpm_pl_spheres(int n, int m, int count, const uint64_t *offsets, const uint16_t *facets,
+                    uint8_t *is_sphere);
+
+/*
  * wpm_candidate_facets with no allocation (the paper has no counterpart: this serves callers
  * that must not allocate, e.g. a service that reserved its device memory at start-up, a host
  * framework whose allocator owns the device, or code running while a stream is captured into

@@ -121,6 +121,9 @@ def lib():
                                        C.POINTER(C.c_double), C.c_void_p]
             L.wpm_iso_classes.argtypes = [C.c_int, C.c_int, u64p, u16p, C.POINTER(C.c_int32)]
             L.wpm_iso_classes.restype = C.c_long
+            L.wpm_pl_spheres.argtypes = [C.c_int, C.c_int, C.c_int, u64p, u16p,
+                                         C.POINTER(C.c_uint8)]
+            L.wpm_pl_spheres.restype = C.c_long
             L.wpm_last_run_stats.argtypes = [C.POINTER(RunStats)]
             L.wpm_release_workspace.argtypes = []
             L.wpm_engine_create.argtypes = [C.POINTER(EngineConfig), C.c_void_p, C.POINTER(C.c_void_p)]
@@ -498,3 +501,17 @@ def iso_classes(m: int, flat, offsets):
     if n < 0:
         raise _err(int(n))
     return cls[:count], int(n)
+
+
+def pl_spheres(n: int, m: int, flat, offsets):
+    """wpm_pl_spheres: (1/0 per complex, number of PL spheres) for complexes given as
+    concatenated facet vertex masks with offsets."""
+    fl = np.ascontiguousarray(flat, dtype=np.uint16)
+    off = np.ascontiguousarray(offsets, dtype=np.uint64)
+    count = off.size - 1
+    out = np.zeros(max(count, 1), dtype=np.uint8)
+    k = lib().wpm_pl_spheres(n, m, count, _p(off, C.c_uint64), _p(fl, C.c_uint16),
+                             _p(out, C.c_uint8))
+    if k < 0:
+        raise _err(int(k))
+    return out[:count].astype(bool), int(k)

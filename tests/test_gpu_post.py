@@ -102,3 +102,30 @@ def test_table2_line15(W, n):
         offs += list(offs[-1] + of[1:].astype(np.int64))
     _, classes = W.iso_classes(n + 4, np.concatenate(flats), np.asarray(offs, dtype=np.uint64))
     assert classes == TABLE2_LINE15[n]
+
+
+TABLE2_LINE19 = {2: 1, 3: 4, 4: 20, 5: 142, 6: 733, 7: 1190, 8: 776, 9: 243, 10: 39}
+
+
+@pytest.mark.parametrize("n", sorted(TABLE2_LINE19))
+def test_table2_line19(W, n):
+    """All of Algorithm 4.4 for n <= 10: GPU enumeration and post-filters, then (host) one
+    representative per isomorphism class and the PL-sphere criterion of Lemma 3.3."""
+    reps = I.idcm_orbit_reps(n)
+    specs = [W.BatchSpec("dual", n, n + 4, r, cap=-2, base_facet=True) for r in reps]
+    counts = [r.count for r in W.enumerate_batch(specs, list_mode=False)]
+    fspecs = [W.BatchSpec("dual", n, n + 4, r, cap=-2, base_facet=True, post_filter=BOTH)
+              for r in reps]
+    res = W.enumerate_batch(fspecs, list_mode=True, capacities=[max(1, c) for c in counts])
+    flats, offs = [], [0]
+    for r, rows in zip(res, reps):
+        fl, of = W.complexes_from_masks(W.candidate_facets("dual", n, n + 4, rows), r.masks)
+        flats.append(fl)
+        offs += list(offs[-1] + of[1:].astype(np.int64))
+    flat, off = np.concatenate(flats), np.asarray(offs, dtype=np.uint64)
+    cls, classes = W.iso_classes(n + 4, flat, off)
+    first = np.unique(cls, return_index=True)[1]
+    rflat = np.concatenate([flat[off[c]:off[c + 1]] for c in first])
+    roff = np.concatenate([[0], np.cumsum([int(off[c + 1] - off[c]) for c in first])])
+    _, spheres = W.pl_spheres(n, n + 4, rflat, roff.astype(np.uint64))
+    assert spheres == TABLE2_LINE19[n]

@@ -55,3 +55,46 @@ def test_iso_classes_of_relabeled_copies():
 def test_iso_classes_input_errors():
     with pytest.raises(wpm.WpmError):
         wpm.iso_classes(6, np.array([1 << 7], dtype=np.uint16), np.array([0, 1], dtype=np.uint64))
+
+
+# ---------------------------------------------------------------------------------------
+# PL sphereness (Algorithm 4.4, line 16) by the library's host routine wpm_pl_spheres
+# ---------------------------------------------------------------------------------------
+
+TABLE2_LINE19 = {2: 1, 3: 4, 4: 20, 5: 142}
+
+
+def _mask(vs):
+    return sum(1 << v for v in vs)
+
+
+def _as_flat(complexes):
+    flat = np.concatenate([np.asarray(K, dtype=np.uint16) for K in complexes])
+    off = np.concatenate([[0], np.cumsum([len(K) for K in complexes])]).astype(np.uint64)
+    return flat, off
+
+
+@pytest.mark.parametrize("n", sorted(TABLE2_LINE19))
+def test_pl_spheres_match_the_oracle(n):
+    flat, off = _complexes(n)
+    cls, count = wpm.iso_classes(n + 4, flat, off)
+    first = [int(np.flatnonzero(cls == c)[0]) for c in range(count)]
+    reps = [flat[off[c]:off[c + 1]] for c in first]
+    got, k = wpm.pl_spheres(n, n + 4, *_as_flat(reps))
+    want = np.array([O.pl_sphere(n, n + 4, K) for K in reps])
+    assert np.array_equal(got, want)
+    assert k == TABLE2_LINE19[n]
+
+
+def test_pl_spheres_closed_cases():
+    import itertools
+    octahedron = [_mask((a, b, c)) for a in (0, 1) for b in (2, 3) for c in (4, 5)]
+    rp2 = [_mask(t) for t in ((0, 1, 2), (0, 2, 3), (0, 3, 4), (0, 4, 5), (0, 5, 1),
+                              (1, 2, 4), (1, 3, 4), (1, 3, 5), (2, 3, 5), (2, 4, 5))]
+    boundary = [_mask(c) for c in itertools.combinations(range(5), 4)]
+    got, k = wpm.pl_spheres(3, 6, *_as_flat([octahedron, rp2]))
+    assert list(got) == [True, False] and k == 1
+    got, _ = wpm.pl_spheres(4, 5, *_as_flat([boundary]))
+    assert list(got) == [True]
+    with pytest.raises(wpm.WpmError):  # a facet of the wrong size
+        wpm.pl_spheres(3, 6, *_as_flat([[_mask((0, 1))]]))
