@@ -285,3 +285,57 @@ def pl_sphere(n, m, facet_masks) -> bool:
     included) is a Z2-homology sphere."""
     kf = np.ascontiguousarray(facet_masks, dtype=np.uint16)
     return bool(_check(lib().orc_pl_sphere(n, m, kf.size, _p(kf, C.c_uint16)), "pl_sphere"))
+
+
+def pic_full(m, facet_masks) -> bool:
+    """Algorithm 4.4 line 9 on its own: K keeps Pic(K) = m - n exactly when its facets use
+    every vertex of [m] (the seedness test of line 10 is not applied)."""
+    used = 0
+    for s in facet_masks:
+        used |= int(s)
+    return used == (1 << m) - 1
+
+
+def link_conditions(n, m, mu, link_facets, apex_row=None):
+    """Section 4.4 (Enumeration for n = 11): the search for the complexes K on [m] whose
+    last vertex a = m - 1 has the link L.
+
+    mu: the dual rows of L's map on the vertices 0..m-2 (distinct nonzero vectors of
+    Z2^(m-n)); apex_row: the dual row of a, by default the one nonzero vector that mu does
+    not take (the paper's case: m = 15 = 2^4 - 1, so the map of K is fixed by mu).
+    Every K with Lk_K(a) = L contains the cone {sigma + a : sigma in L}, so
+      condition (1): each facet sigma + a (sigma a facet of L) is in K;
+      condition (2): each other candidate facet through a is not in K.
+    Returns (the m dual rows of K's map, its candidate facets, forced-in mask, forced-out
+    mask), the masks as ceil(M/64) uint64 words over the candidate facets."""
+    p = m - n
+    mu = [int(v) for v in mu]
+    assert len(mu) == m - 1
+    if apex_row is None:
+        missing = [v for v in range(1, 1 << p) if v not in mu]
+        assert len(missing) == 1, "the apex row is fixed by mu only when mu misses one vector"
+        apex_row = missing[0]
+    lam = mu + [int(apex_row)]
+    facets = candidate_facets("dual", n, m, lam)
+    a = 1 << (m - 1)
+    cone = set()
+    for s in link_facets:
+        s = int(s)
+        assert bin(s).count("1") == n - 1 and s < a, "a facet of L is an (n-1)-subset of [m-1]"
+        cone.add(s | a)
+    W = max(1, (len(facets) + 63) // 64)
+    fin = np.zeros(W, dtype=np.uint64)
+    fout = np.zeros(W, dtype=np.uint64)
+    seen = 0
+    for j, s in enumerate(facets):
+        s = int(s)
+        if not s & a:
+            continue
+        bit = np.uint64(1 << (j % 64))
+        if s in cone:
+            fin[j // 64] |= bit
+            seen += 1
+        else:
+            fout[j // 64] |= bit
+    assert seen == len(cone), "every cone facet sigma + a must be a candidate facet of K's map"
+    return lam, facets, fin, fout

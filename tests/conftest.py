@@ -33,3 +33,23 @@ def gpu_available():
         return torch.cuda.is_available()
     except Exception:
         return False
+
+
+def load_n11_seeds():
+    """tests/golden/n11_seeds.txt (written by make_n11_seeds.py from the oracle alone):
+    (totals dict, classes [(members, is_sphere, facets)], samples [(orbit, link mask words,
+    count, nodes, probes, kept)])."""
+    totals, classes, samples = {}, [], []
+    with open(os.path.join(GOLDEN, "n11_seeds.txt")) as fh:
+        for line in fh:
+            t = line.split()
+            if not t or t[0].startswith("#"):
+                continue
+            if t[0] == "class":
+                classes.append((int(t[1]), bool(int(t[2])), [int(x, 16) for x in t[3:]]))
+            elif t[0] == "sample":
+                samples.append((int(t[1]), [int(x, 16) for x in t[2:-4]],
+                                *[int(x) for x in t[-4:]]))
+            else:
+                totals[t[0]] = int(t[1])
+    return totals, classes, samples
