@@ -279,6 +279,30 @@ long wpm_pl_spheres(int n, int m, int count, const uint64_t *offsets, const uint
                     uint8_t *is_sphere);
 
 /*
+ * Link conditions of the n = 11 construction (Section 4.4, "Enumeration for n = 11",
+ * conditions (1) and (2) on X). A complex K on [m] whose last vertex a = m - 1 has the link
+ * L contains the cone {sigma + a : sigma a facet of L}; K is searched for with
+ *   forced_in  = the cone facets sigma + a                              (condition (1)),
+ *   forced_out = every other candidate facet of K's map through a      (condition (2)).
+ * Inputs (host pointers, read during the call): n (facet size of K) and m (its vertices;
+ * K's map is dual, of Picard number m - n); mu_rows[0..m-1): the dual rows of L's map on the
+ * vertices 0..m-2 (nonzero, distinct vectors of Z2^(m-n)); apex_row: the dual row of a, or 0
+ * for the one nonzero vector that mu does not take (the paper's case m = 15 = 2^4 - 1, where
+ * mu fixes K's map); link_facets[0..link_count): L's facets as vertex masks, (n-1)-subsets of
+ * [m-1]. Outputs (host, caller-owned): lambda_rows_out[0..m): K's dual map (mu, then the apex
+ * row); forced_in and forced_out: `words` uint64 words each, over K's candidate facets in the
+ * library's order (words beyond ceil(M/64) are zeroed). Returns M, the candidate facets of
+ * K's map (the n_facets to pass in wpm_conditions with the masks), or WPM_ERR_INPUT (sizes,
+ * zero or repeated rows, rank < m - n, apex_row 0 with mu missing other than one vector, a
+ * link facet of the wrong size, through a, repeated, or whose cone facet is not a candidate,
+ * i.e. L does not support mu), WPM_ERR_CAPACITY (words < ceil(M/64); nothing written),
+ * WPM_ERR_LIMIT (M > WPM_MAX_FACETS). Computed on the host; runs without a GPU.
+ */
+int wpm_link_conditions(int n, int m, const uint32_t *mu_rows, uint32_t apex_row,
+                        const uint16_t *link_facets, int link_count, uint32_t *lambda_rows_out,
+                        uint64_t *forced_in, uint64_t *forced_out, int words);
+
+/*
  * wpm_candidate_facets with no allocation (the paper has no counterpart: this serves callers
  * that must not allocate, e.g. a service that reserved its device memory at start-up, a host
  * framework whose allocator owns the device, or code running while a stream is captured into

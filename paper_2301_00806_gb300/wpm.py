@@ -34,6 +34,7 @@ MODE_LIST = 0
 MODE_COUNT = 1
 CAP_NONE = -1
 CAP_UBT = -2
+MAX_FACETS = 2048  # WPM_MAX_FACETS
 
 _KIND = {"primal": PRIMAL, "dual": DUAL, PRIMAL: PRIMAL, DUAL: DUAL}
 
@@ -124,6 +125,8 @@ def lib():
             L.wpm_pl_spheres.argtypes = [C.c_int, C.c_int, C.c_int, u64p, u16p,
                                          C.POINTER(C.c_uint8)]
             L.wpm_pl_spheres.restype = C.c_long
+            L.wpm_link_conditions.argtypes = [C.c_int, C.c_int, u32p, C.c_uint32, u16p, C.c_int,
+                                              u32p, u64p, u64p, C.c_int]
             L.wpm_last_run_stats.argtypes = [C.POINTER(RunStats)]
             L.wpm_release_workspace.argtypes = []
             L.wpm_engine_create.argtypes = [C.POINTER(EngineConfig), C.c_void_p, C.POINTER(C.c_void_p)]
@@ -515,3 +518,25 @@ def pl_spheres(n: int, m: int, flat, offsets):
     if k < 0:
         raise _err(int(k))
     return out[:count].astype(bool), int(k)
+
+
+def link_conditions(n: int, m: int, mu_rows: Sequence[int], link_facets, apex_row: int = 0):
+    """wpm_link_conditions (Section 4.4, conditions (1) and (2)): for the link L (facet
+    vertex masks on [m-1]) of the apex m - 1 under the dual map mu_rows (m - 1 rows), returns
+    (K's m dual rows, M, forced_in, forced_out) with the masks as ceil(M/64) uint64 words over
+    K's candidate facets. apex_row 0: the one nonzero vector mu misses."""
+    mu = np.ascontiguousarray(mu_rows, dtype=np.uint32)
+    if mu.size != m - 1:
+        raise WpmError(ERR_INPUT, f"mu has {mu.size} rows, m - 1 = {m - 1} needed")
+    lf = np.ascontiguousarray(link_facets, dtype=np.uint16)
+    lam = np.zeros(m, dtype=np.uint32)
+    words = MAX_FACETS // 64
+    fin = np.zeros(words, dtype=np.uint64)
+    fout = np.zeros(words, dtype=np.uint64)
+    M = lib().wpm_link_conditions(n, m, _p(mu, C.c_uint32), apex_row, _p(lf, C.c_uint16),
+                                  lf.size, _p(lam, C.c_uint32), _p(fin, C.c_uint64),
+                                  _p(fout, C.c_uint64), words)
+    if M < 0:
+        raise _err(M)
+    W = max(1, (M + 63) // 64)
+    return [int(x) for x in lam], int(M), fin[:W].copy(), fout[:W].copy()
