@@ -12,7 +12,17 @@
 // Every step depends on invariants only, so isomorphic complexes get equal forms; equal
 // mixes of different data only merge colours, which widens the search without changing the
 // form. Classes are numbered in order of first appearance.
+//
+// Automorphism pruning. Two leaves with equal relabeled facet lists give an automorphism g
+// of K (one leaf's labeling followed by the inverse of the other's). If g fixes the vertices
+// individualized above a node and maps an explored child u of that node to a child v, the
+// subtrees of u and v have the same leaves up to g, so v is skipped; when a new automorphism
+// shows that the child being searched is such a v, the search returns to that node at once.
+// Pruning removes only subtrees whose leaves have all been seen, so forms are unchanged; it
+// turns searches over highly symmetric complexes (joins, suspensions, wedges), whose
+// automorphism groups have up to ~10^5 elements, from exponential into a few hundred leaves.
 #include <algorithm>
+#include <array>
 #include <cstdint>
 #include <cstring>
 #include <mutex>
@@ -34,6 +44,14 @@ inline uint64_t mix64(uint64_t x) {  // a bijective 64-bit finaliser
   x ^= x >> 33;
   return x;
 }
+
+struct FormHash {
+  size_t operator()(const std::vector<uint16_t> &v) const {
+    uint64_t h = 0x243f6a8885a308d3ull ^ v.size();
+    for (uint16_t x : v) h = mix64(h ^ x);
+    return (size_t)h;
+  }
+};
 
 struct Canon {
   int m = 0;
@@ -77,7 +95,42 @@ struct Canon {
     }
   }
 
-  void search(int *col) {
+  // search state: path[d] = vertex individualized at depth d, done[d] = explored children
+  // of the node at depth d (bit v), autos = automorphisms found, seen = leaf forms found
+  int path[16] = {0};
+  uint32_t done[17] = {0};
+  std::vector<std::array<uint8_t, 16>> autos;
+  std::unordered_map<std::vector<uint16_t>, std::array<uint8_t, 16>, FormHash> seen;
+  static constexpr size_t kMaxAutos = 64, kMaxSeen = 4096;
+
+  // 1 when v is in the orbit of a vertex of `set` under the group generated by the known
+  // automorphisms that fix path[0..depth) pointwise
+  bool orbit_hits(int v, uint32_t set, int depth) const {
+    if (!set) return false;
+    int parent[16];
+    for (int u = 0; u < m; u++) parent[u] = u;
+    auto find = [&](int x) {
+      while (parent[x] != x) x = parent[x] = parent[parent[x]];
+      return x;
+    };
+    for (const auto &g : autos) {
+      bool fixes = true;
+      for (int d = 0; d < depth && fixes; d++) fixes = g[path[d]] == path[d];
+      if (!fixes) continue;
+      for (int u = 0; u < m; u++) {
+        const int a = find(u), b = find(g[u]);
+        if (a != b) parent[a] = b;
+      }
+    }
+    const int r = find(v);
+    for (int u = 0; u < m; u++)
+      if (((set >> u) & 1u) && find(u) == r) return true;
+    return false;
+  }
+
+  // Searches the node at `depth`; returns -1, or the depth of an ancestor whose current
+  // child turned out equivalent to an explored one (the search resumes there).
+  int search(int *col, int depth) {
     refine(col);
     int cnt[16] = {0};
     for (int v = 0; v < m; v++) cnt[col[v]]++;
@@ -100,25 +153,44 @@ struct Canon {
         best = leaf;
         have = true;
       }
-      return;
+      std::array<uint8_t, 16> lab{};
+      for (int v = 0; v < m; v++) lab[v] = (uint8_t)col[v];
+      auto it = seen.find(leaf);
+      if (it == seen.end()) {
+        if (seen.size() < kMaxSeen) seen.emplace(leaf, lab);
+        return -1;
+      }
+      // equal forms: g = (the earlier leaf's labeling)^-1 o (this leaf's labeling)
+      int inv[16];
+      for (int v = 0; v < m; v++) inv[it->second[v]] = v;
+      std::array<uint8_t, 16> g{};
+      bool identity = true;
+      for (int v = 0; v < m; v++) {
+        g[v] = (uint8_t)inv[lab[v]];
+        identity = identity && g[v] == v;
+      }
+      if (identity || autos.size() >= kMaxAutos) return -1;
+      autos.push_back(g);
+      for (int d = 0; d < depth; d++)
+        if (orbit_hits(path[d], done[d], d)) return d;
+      return -1;
     }
+    done[depth] = 0;
     for (int v = 0; v < m; v++) {
       if (col[v] != target) continue;
+      if (orbit_hits(v, done[depth], depth)) continue;
       int c2[16];
       for (int u = 0; u < m; u++)
         c2[u] = col[u] > target ? col[u] + 1 : (col[u] == target && u != v ? target + 1 : col[u]);
-      search(c2);
+      path[depth] = v;
+      const int r = search(c2, depth + 1);
+      done[depth] |= 1u << v;
+      if (r >= 0 && r < depth) return r;
     }
+    return -1;
   }
 };
 
-struct FormHash {
-  size_t operator()(const std::vector<uint16_t> &v) const {
-    uint64_t h = 0x243f6a8885a308d3ull ^ v.size();
-    for (uint16_t x : v) h = mix64(h ^ x);
-    return (size_t)h;
-  }
-};
 
 }  // namespace
 }  // namespace wpm
@@ -144,7 +216,7 @@ extern "C" long wpm_iso_classes(int m, int count, const uint64_t *offsets,
       C.f = facets + offsets[c];
       C.k = (int)(offsets[c + 1] - offsets[c]);
       int col[16] = {0};
-      C.search(col);
+      C.search(col, 0);
       form[c] = std::move(C.best);
     }
   };

@@ -52,6 +52,71 @@ def test_iso_classes_of_relabeled_copies():
     assert np.array_equal(cls[0::2], cls[1::2])
 
 
+def _pic_only_complexes(n, stride):
+    """Every stride-th line-7 WPM of n (base facet and cap, all IDCM orbits) that uses all
+    n + 4 vertices, without the seedness filter: wedges, suspensions and joins included,
+    whose automorphism groups are large."""
+    flats, offs = [], [0]
+    k = 0
+    for rows in I.idcm_orbit_reps(n):
+        f = O.candidate_facets("dual", n, n + 4, rows)
+        c, _, _, masks = O.enumerate_dfs(n, n + 4, f, cap=-2, base_facet=True,
+                                         capacity=1 << 17)
+        for i in range(c):
+            K = O.masks_to_facets(f, masks[i])
+            if not O.pic_full(n + 4, K):
+                continue
+            if k % stride == 0:
+                flats.append(np.asarray(K, dtype=np.uint16))
+                offs.append(offs[-1] + len(K))
+            k += 1
+    return np.concatenate(flats), np.asarray(offs, dtype=np.uint64)
+
+
+@pytest.mark.parametrize("n,stride", [(3, 1), (4, 3)])
+def test_iso_classes_of_symmetric_complexes_match_the_oracle(n, stride):
+    flat, off = _pic_only_complexes(n, stride)
+    cls, count = wpm.iso_classes(n + 4, flat, off)
+    forms, want = {}, []
+    for c in range(off.size - 1):
+        f = O.canonical_form(n + 4, flat[off[c]:off[c + 1]])
+        want.append(forms.setdefault(f, len(forms)))
+    assert count == len(forms)
+    assert np.array_equal(cls, np.asarray(want, dtype=np.int32))
+
+
+def _join(*parts):
+    """Facets of the join of the boundaries of simplices with the given vertex counts."""
+    import itertools
+    blocks, v = [], 0
+    for size in parts:
+        verts = list(range(v, v + size))
+        blocks.append([sum(1 << u for u in verts if u != w) for w in verts])
+        v += size
+    return [sum(c) for c in itertools.product(*blocks)], v
+
+
+@pytest.mark.parametrize("parts_a,parts_b", [((2, 2, 5, 5), (2, 3, 4, 5)),
+                                             ((3, 3, 4, 4), (2, 4, 4, 4)),
+                                             ((2, 2, 2, 2, 2, 2, 2), (2, 2, 2, 2, 2, 4))])
+def test_iso_classes_of_joins(parts_a, parts_b):
+    """Joins of simplex boundaries (automorphism groups up to 2^7 7! = 645,120): seeded
+    relabelings of one join share a class, another join on as many vertices does not."""
+    A, m = _join(*parts_a)
+    B, mb = _join(*parts_b)
+    assert m == mb
+    rng = np.random.default_rng(m)
+    complexes = []
+    for X in (A, B):
+        for _ in range(4):
+            perm = rng.permutation(m)
+            complexes.append([sum(1 << int(perm[u]) for u in range(m) if (F >> u) & 1)
+                              for F in X])
+    cls, count = wpm.iso_classes(m, *_as_flat(complexes))
+    assert count == 2
+    assert len(set(cls[:4])) == 1 and len(set(cls[4:])) == 1 and cls[0] != cls[4]
+
+
 def test_iso_classes_input_errors():
     with pytest.raises(wpm.WpmError):
         wpm.iso_classes(6, np.array([1 << 7], dtype=np.uint16), np.array([0, 1], dtype=np.uint64))
