@@ -18,6 +18,8 @@ path (candidate facets, ridges, search, per-instance sort) over the 4096 instanc
          algorithm: context only)
   paper_table2  Algorithm 4.4 end to end for n = 2..10 (all four printed rows of Table 2),
          checked against the paper's counts, seconds per n
+  paper_n11  Section 4.4's n = 11 construction end to end (114 links, then the paper's
+         4 seeds), checked against the paper's counts, seconds
   serving  the request loop over the serving engine (continuous batching): Poisson
          arrivals at 200 jobs/s for 60 s, n uniform in {5..9}, each job's full sorted list;
          p50/p99 latency (completion - arrival) over the jobs finished by the deadline,
@@ -208,43 +210,55 @@ TABLE2 = {  # Table 2 of the paper: |K(n,4)| at lines 7 and 13, |K°(n,4)| at li
 
 
 def run_paper_table2(stream):
-    """Algorithm 4.4 end to end for n = 2..10: one map per IDCM orbit with the base facet and
-    the cap (GPU), the post-filters Pic(K) = 4 and seedness (GPU), one representative per
-    isomorphism class and the PL-sphere test of Lemma 3.3 (host). Each n timed end to end."""
-    import numpy as np
+    """Algorithm 4.4 end to end for n = 2..10 (seeds.colorable_seeds): one map per IDCM orbit
+    with the base facet and the cap (GPU), the post-filters Pic(K) = 4 and seedness (GPU),
+    one representative per isomorphism class and the PL-sphere test of Lemma 3.3 (host).
+    Each n timed end to end."""
     import torch
-    from paper_2301_00806_gb300 import instances as I, wpm
+    from paper_2301_00806_gb300 import seeds
     rows, total = [], 0.0
     for n in sorted(TABLE2):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        reps = I.idcm_orbit_reps(n)
-        specs = [wpm.BatchSpec("dual", n, n + 4, r, cap=wpm.CAP_UBT, base_facet=True)
-                 for r in reps]
-        line7 = [r.count for r in wpm.enumerate_batch(specs, list_mode=False, stream=stream)]
-        fspecs = [wpm.BatchSpec("dual", n, n + 4, r, cap=wpm.CAP_UBT, base_facet=True,
-                                post_filter=wpm.POST_PIC | wpm.POST_SEED) for r in reps]
-        res = wpm.enumerate_batch(fspecs, list_mode=True, capacities=[max(1, c) for c in line7],
-                                  stream=stream)
-        flats, offs = [], [0]
-        for r, rr in zip(res, reps):
-            fl, of = wpm.complexes_from_masks(wpm.candidate_facets("dual", n, n + 4, rr), r.masks)
-            flats.append(fl)
-            offs += list(offs[-1] + of[1:].astype(np.int64))
-        flat, off = np.concatenate(flats), np.asarray(offs, dtype=np.uint64)
-        cls, classes = wpm.iso_classes(n + 4, flat, off)
-        first = np.unique(cls, return_index=True)[1]
-        rflat = np.concatenate([flat[off[c]:off[c + 1]] for c in first])
-        roff = np.concatenate([[0], np.cumsum([int(off[c + 1] - off[c]) for c in first])])
-        _, spheres = wpm.pl_spheres(n, n + 4, rflat, roff.astype(np.uint64))
+        run = seeds.colorable_seeds(n, stream=stream)
         dt = time.perf_counter() - t0
         total += dt
-        got = (sum(line7), int(off.size - 1), classes, spheres)
+        got = (run.line7, run.line13, run.line15, run.line19)
         rows.append({"n": n, "lines_7_13_15_19": list(got), "paper": list(TABLE2[n]),
                      "exact": got == TABLE2[n], "seconds": dt})
     return {"workload": "Algorithm 4.4 for n = 2..10: one map per IDCM orbit, base facet and "
                         "cap, post-filters (GPU), isomorphism classes and PL spheres (host)",
             "all_exact": all(r["exact"] for r in rows), "seconds_total": total, "rows": rows}
+
+
+def run_paper_n11(stream):
+    """Section 4.4's n = 11 construction end to end (seeds.colorable_seeds_n11): the n = 10
+    run without the seedness discard gives the links (the paper: 114 PL spheres, 39 of them
+    seeds); one conditioned n = 11 search per link, then Algorithm 4.4's filters (the paper's
+    Theorem: exactly 4 seeds)."""
+    import torch
+    from paper_2301_00806_gb300 import seeds
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    links, run = seeds.colorable_seeds_n11(stream=stream)
+    dt = time.perf_counter() - t0
+    return {"workload": "n = 10 links (3 IDCM orbits, base facet and cap, Pic(K) = 4, "
+                        "classes, PL spheres), then one cone-conditioned n = 11 search per link "
+                        "with the cap, post-filters, classes and PL spheres",
+            "links": links.line19, "n11_wpms": run.line7, "n11_pic_seed": run.line13,
+            "n11_classes": run.line15, "n11_seeds": run.line19,
+            "paper": {"links": 114, "n11_seeds": 4},
+            "exact": links.line19 == 114 and run.line19 == 4,
+            "nodes": links.nodes + run.nodes, "seconds": dt,
+            "seconds_links": links.seconds, "seconds_n11": run.seconds}
+
+
+def _guarded(fn, *args):
+    """An extra section's result, or its error (the main line is printed either way)."""
+    try:
+        return fn(*args)
+    except Exception as e:  # noqa: BLE001
+        return {"error": f"{type(e).__name__}: {e}"}
 
 
 def run_paper_table1(stream):
@@ -430,7 +444,8 @@ def run_ours(args, rank, world):
     if world == 1 and args.table1:
         line["plain_configs"] = run_plain_configs(stream)
         line["paper_table1"] = run_paper_table1(stream)
-        line["paper_table2"] = run_paper_table2(stream)
+        line["paper_table2"] = _guarded(run_paper_table2, stream)
+        line["paper_n11"] = _guarded(run_paper_n11, stream)
     if world == 1 and args.serve_seconds > 0:
         line["serving"] = run_serving(args)
     return line

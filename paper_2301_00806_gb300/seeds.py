@@ -1,0 +1,143 @@
+"""Algorithm 4.4 (the Z2^n-colorable seeds of Picard number 4) and the n = 11 construction
+of Section 4.4, as sequences of library calls.
+
+Every step is a call into libwpm: the searches and the post-filters of lines 8-12 run on
+the GPU (wpm_enumerate_batch), the link conditions (wpm_link_conditions), isomorphism
+classes (line 14, wpm_iso_classes) and the PL-sphere test (line 16, wpm_pl_spheres) in its
+native host code. This module only hands each call's output to the next.
+
+  colorable_seeds(n)          lines 1-19 for one n <= 10: one map per IDCM orbit
+                              (Proposition 4.3), the base facet and the cap (line 5),
+                              Pic(K) = 4 and seedness (lines 8-12), one K per class (14),
+                              PL spheres (15-19). seedness=False skips line 10, which gives
+                              the links that Section 4.4 starts from.
+  seeds_from_links(links, n)  Section 4.4's construction for dimension n - 1: for each link
+                              L with its map mu, K's map (mu plus the apex row) and the cone
+                              conditions (1), (2); then lines 5-19 of Algorithm 4.4 on the
+                              conditioned searches.
+  colorable_seeds_n11()       the paper's n = 11 run: the 114 PL spheres of n = 10 (seeds
+                              and non-seeds) as links, one map each, then seeds_from_links.
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field
+from typing import List, Sequence, Tuple
+
+import numpy as np
+
+from . import instances as I
+from . import wpm
+
+
+@dataclass
+class SeedRun:
+    """Counts at the lines of Algorithm 4.4, and one complex per PL-sphere class."""
+    n: int
+    maps: int                      # maps searched (IDCM orbits, or links)
+    line7: int                     # WPMs found by the searches
+    line13: int                    # after Pic(K) = 4 (and seedness, when applied)
+    line15: int                    # isomorphism classes
+    line19: int                    # PL spheres among them
+    spheres: List[Tuple[List[int], np.ndarray]] = field(default_factory=list)
+    # (dual rows of the map the representative was found for, its facet vertex masks)
+    nodes: int = 0                 # search nodes of the canonical trees
+    seconds: float = 0.0
+
+
+class _Found:
+    """The complexes that passed, all maps together: facets flat[off[c]:off[c+1]] of
+    complex c, found for the map rows[owner[c]]."""
+
+    def __init__(self):
+        self.rows, self.flats, self.offs, self.owner = [], [], [0], []
+
+    def add(self, rows, flat, off):
+        k = len(self.rows)
+        self.rows.append(rows)
+        self.flats.append(flat)
+        base = self.offs[-1]
+        self.offs += [base + int(x) for x in off[1:]]
+        self.owner += [k] * (off.size - 1)
+
+    def arrays(self):
+        flat = np.concatenate(self.flats) if self.flats else np.zeros(0, dtype=np.uint16)
+        return flat.astype(np.uint16), np.asarray(self.offs, dtype=np.uint64)
+
+
+def _classes_and_spheres(n: int, m: int, found: _Found):
+    """-> (classes, [(map rows, facets) of one member of each PL-sphere class])."""
+    flat, off = found.arrays()
+    if off.size == 1:
+        return 0, []
+    cls, classes = wpm.iso_classes(m, flat, off)
+    first = sorted(np.unique(cls, return_index=True)[1])  # first member of each class
+    reps = [flat[off[c]:off[c + 1]].copy() for c in first]
+    rflat = np.concatenate(reps).astype(np.uint16)
+    roff = np.concatenate([[0], np.cumsum([len(K) for K in reps])]).astype(np.uint64)
+    is_sphere, _ = wpm.pl_spheres(n, m, rflat, roff)
+    return classes, [(found.rows[found.owner[c]], K)
+                     for c, K, s in zip(first, reps, is_sphere) if s]
+
+
+def _search(specs: List[wpm.BatchSpec], post: int, stream=None):
+    """Counting run (line 7) then list run with the post-filters; returns (line-7 count,
+    nodes, the complexes that pass)."""
+    counted = wpm.enumerate_batch(specs, list_mode=False, stream=stream)
+    for r in counted:
+        if r.status != wpm.OK:
+            raise wpm.WpmError(r.status, "counting run failed")
+    listed_specs = [wpm.BatchSpec(s.kind, s.n, s.m, s.cols, cap=s.cap, base_facet=s.base_facet,
+                                  forced_in=s.forced_in, forced_out=s.forced_out,
+                                  n_facets=s.n_facets, post_filter=post) for s in specs]
+    listed = wpm.enumerate_batch(listed_specs, list_mode=True,
+                                 capacities=[max(1, r.count) for r in counted], stream=stream)
+    found = _Found()
+    for s, r in zip(specs, listed):
+        if r.status != wpm.OK:
+            raise wpm.WpmError(r.status, "list run failed")
+        if r.count == 0:
+            continue
+        facets = wpm.candidate_facets(s.kind, s.n, s.m, s.cols)
+        flat, off = wpm.complexes_from_masks(facets, r.masks)
+        found.add([int(x) for x in s.cols], flat, off)
+    return sum(r.count for r in counted), sum(r.nodes for r in counted), found
+
+
+def colorable_seeds(n: int, seedness: bool = True, stream=None) -> SeedRun:
+    """Algorithm 4.4 for 2 <= n <= 10 (m = n + 4)."""
+    t0 = time.perf_counter()
+    reps = I.idcm_orbit_reps(n)
+    specs = [wpm.BatchSpec("dual", n, n + 4, r, cap=wpm.CAP_UBT, base_facet=True) for r in reps]
+    post = wpm.POST_PIC | (wpm.POST_SEED if seedness else 0)
+    line7, nodes, found = _search(specs, post, stream)
+    classes, spheres = _classes_and_spheres(n, n + 4, found)
+    return SeedRun(n, len(reps), line7, len(found.owner), classes, len(spheres), spheres, nodes,
+                   time.perf_counter() - t0)
+
+
+def seeds_from_links(links: Sequence[Tuple[Sequence[int], Sequence[int]]], n: int,
+                     stream=None) -> SeedRun:
+    """Section 4.4's construction: the seeds K of dimension n - 1 on m = n + 4 vertices
+    whose apex m - 1 has one of the given links. links: [(mu, L)], mu the m - 1 dual rows
+    of L's map, L its facets (vertex masks on [m - 1]); K's map is mu plus the one nonzero
+    vector of Z2^4 that mu misses (so m = 15, n = 11)."""
+    t0 = time.perf_counter()
+    m = n + 4
+    specs = []
+    for mu, L in links:
+        lam, M, fin, fout = wpm.link_conditions(n, m, mu, L)
+        specs.append(wpm.BatchSpec("dual", n, m, lam, cap=wpm.CAP_UBT, forced_in=fin,
+                                   forced_out=fout, n_facets=M))
+    line7, nodes, found = _search(specs, wpm.POST_PIC | wpm.POST_SEED, stream)
+    classes, spheres = _classes_and_spheres(n, m, found)
+    return SeedRun(n, len(specs), line7, len(found.owner), classes, len(spheres), spheres, nodes,
+                   time.perf_counter() - t0)
+
+
+def colorable_seeds_n11(stream=None) -> Tuple[SeedRun, SeedRun]:
+    """The paper's n = 11 run: (the n = 10 run without the seedness discard, whose PL
+    spheres are the links; the n = 11 run from those links)."""
+    links = colorable_seeds(10, seedness=False, stream=stream)
+    run = seeds_from_links([(rows, K) for rows, K in links.spheres], 11, stream=stream)
+    return links, run
