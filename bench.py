@@ -20,6 +20,8 @@ path (candidate facets, ridges, search, per-instance sort) over the 4096 instanc
          checked against the paper's counts, seconds per n
   paper_n11  Section 4.4's n = 11 construction end to end (114 links, then the paper's
          4 seeds), checked against the paper's counts, seconds
+  paper_main_theorem  the main theorem's Picard-4 row assembled from the two runs above
+         (plus Section 4.3's cross-polytope at n = 4): total against the paper's 3153
   serving  the request loop over the serving engine (continuous batching): Poisson
          arrivals at 200 jobs/s for 60 s, n uniform in {5..9}, each job's full sorted list;
          p50/p99 latency (completion - arrival) over the jobs finished by the deadline,
@@ -253,6 +255,21 @@ def run_paper_n11(stream):
             "seconds_links": links.seconds, "seconds_n11": run.seconds}
 
 
+def run_main_theorem(table2, n11, stream):
+    """The main theorem's Picard-4 row from the two runs above: Table 2's line 19 per n,
+    Section 4.3's cross-polytope at n = 4 (checked: a PL sphere isomorphic to none of the
+    n = 4 classes), the n = 11 seeds; its total against the paper's 3153."""
+    from paper_2301_00806_gb300 import seeds
+    row = {r["n"]: r["lines_7_13_15_19"][3] for r in table2["rows"]}
+    extra = seeds.extra_n4_seed(seeds.colorable_seeds(4, stream=stream))
+    row[4] += int(extra)
+    row[11] = n11["n11_seeds"]
+    want = seeds.MAIN_THEOREM_P4
+    return {"row": {str(k): v for k, v in sorted(row.items())}, "total": sum(row.values()),
+            "paper_total": sum(want.values()), "cross_polytope_added": extra,
+            "exact": row == want}
+
+
 def _guarded(fn, *args):
     """An extra section's result, or its error (the main line is printed either way)."""
     try:
@@ -446,6 +463,9 @@ def run_ours(args, rank, world):
         line["paper_table1"] = run_paper_table1(stream)
         line["paper_table2"] = _guarded(run_paper_table2, stream)
         line["paper_n11"] = _guarded(run_paper_n11, stream)
+        if "rows" in line["paper_table2"] and "n11_seeds" in line["paper_n11"]:
+            line["paper_main_theorem"] = _guarded(run_main_theorem, line["paper_table2"],
+                                                  line["paper_n11"], stream)
     if world == 1 and args.serve_seconds > 0:
         line["serving"] = run_serving(args)
     return line

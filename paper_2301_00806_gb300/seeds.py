@@ -141,3 +141,45 @@ def colorable_seeds_n11(stream=None) -> Tuple[SeedRun, SeedRun]:
     links = colorable_seeds(10, seedness=False, stream=stream)
     run = seeds_from_links([(rows, K) for rows, K in links.spheres], 11, stream=stream)
     return links, run
+
+
+def cross_polytope_boundary(d: int) -> np.ndarray:
+    """Facets (vertex masks) of the boundary of the d-dimensional cross-polytope, antipodal
+    vertices 2i and 2i + 1: one vertex of each pair."""
+    facets = []
+    for bits in range(1 << d):
+        facets.append(sum(1 << (2 * i + ((bits >> i) & 1)) for i in range(d)))
+    return np.asarray(sorted(facets), dtype=np.uint16)
+
+
+def extra_n4_seed(run4: SeedRun) -> bool:
+    """Section 4.3's addition to n = 4: the boundary of the 4-dimensional cross-polytope, a
+    seed of Picard number 4 that supports a dual characteristic map but no injective one, so
+    the IDCM runs cannot find it. True when it is a PL sphere (Lemma 3.3) isomorphic to none
+    of the PL-sphere classes of run4 (Algorithm 4.4 for n = 4)."""
+    K = cross_polytope_boundary(4)
+    is_sphere, _ = wpm.pl_spheres(4, 8, K, np.asarray([0, K.size], dtype=np.uint64))
+    reps = [F for _, F in run4.spheres] + [K]
+    flat = np.concatenate(reps).astype(np.uint16)
+    off = np.concatenate([[0], np.cumsum([len(F) for F in reps])]).astype(np.uint64)
+    cls, classes = wpm.iso_classes(8, flat, off)
+    return bool(is_sphere[0]) and classes == len(run4.spheres) + 1 and \
+        int(cls[-1]) == len(run4.spheres)
+
+
+# The main theorem's Picard-4 row: Z2^n-colorable seeds of dimension n - 1 up to isomorphism
+MAIN_THEOREM_P4 = {2: 1, 3: 4, 4: 21, 5: 142, 6: 733, 7: 1190, 8: 776, 9: 243, 10: 39, 11: 4}
+
+
+def main_theorem_p4(ns: Sequence[int] = tuple(range(2, 11)), n11: bool = True,
+                    stream=None) -> dict:
+    """The main theorem's row for Picard number 4: Algorithm 4.4's PL spheres (line 19) for
+    each n in ns, plus Section 4.3's cross-polytope at n = 4, plus (n11) the seeds of the
+    n = 11 construction. Returns {n: count}."""
+    row = {}
+    for n in ns:
+        run = colorable_seeds(n, stream=stream)
+        row[n] = run.line19 + (int(extra_n4_seed(run)) if n == 4 else 0)
+    if n11:
+        row[11] = colorable_seeds_n11(stream=stream)[1].line19
+    return row

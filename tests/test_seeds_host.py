@@ -99,3 +99,19 @@ def test_bench_table2_section(on_oracle, monkeypatch):
     out = bench.run_paper_table2(None)
     assert out["all_exact"] and [r["n"] for r in out["rows"]] == [2, 3, 4]
     assert "error" in bench._guarded(lambda: 1 / 0)
+
+
+def test_main_theorem_row_small_n(on_oracle):
+    row = seeds.main_theorem_p4(ns=(2, 3, 4), n11=False)
+    assert row == {n: seeds.MAIN_THEOREM_P4[n] for n in (2, 3, 4)}
+    K = seeds.cross_polytope_boundary(4)
+    assert len(K) == 16 and O.pic_seed(4, 8, K) and O.pl_sphere(4, 8, K)
+
+
+def test_bench_main_theorem_section(on_oracle):
+    import bench
+    table2 = {"rows": [{"n": n, "lines_7_13_15_19": [0, 0, 0, seeds.MAIN_THEOREM_P4[n]]}
+                       for n in range(2, 11)]}
+    table2["rows"][2]["lines_7_13_15_19"][3] -= 1      # Table 2 prints 20 at n = 4
+    out = bench.run_main_theorem(table2, {"n11_seeds": 4}, None)
+    assert out["exact"] and out["total"] == 3153 and out["cross_polytope_added"]
