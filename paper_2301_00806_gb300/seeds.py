@@ -83,6 +83,8 @@ def _classes_and_spheres(n: int, m: int, found: _Found):
 def _search(specs: List[wpm.BatchSpec], post: int, stream=None):
     """Counting run (line 7) then list run with the post-filters; returns (line-7 count,
     nodes, the complexes that pass)."""
+    if not specs:
+        return 0, 0, _Found()
     counted = wpm.enumerate_batch(specs, list_mode=False, stream=stream)
     for r in counted:
         if r.status != wpm.OK:

@@ -115,3 +115,9 @@ def test_bench_main_theorem_section(on_oracle):
     table2["rows"][2]["lines_7_13_15_19"][3] -= 1      # Table 2 prints 20 at n = 4
     out = bench.run_main_theorem(table2, {"n11_seeds": 4}, None)
     assert out["exact"] and out["total"] == 3153 and out["cross_polytope_added"]
+
+
+def test_seeds_from_no_links(on_oracle):
+    run = seeds.seeds_from_links([], 11)
+    assert (run.maps, run.line7, run.line13, run.line15, run.line19) == (0, 0, 0, 0, 0)
+    assert run.spheres == []
