@@ -163,3 +163,28 @@ def test_pl_spheres_closed_cases():
     assert list(got) == [True]
     with pytest.raises(wpm.WpmError):  # a facet of the wrong size
         wpm.pl_spheres(3, 6, *_as_flat([[_mask((0, 1))]]))
+
+
+def test_n11_stored_classes_through_the_host_routines():
+    """The oracle's n = 11 classes (make_n11_seeds.py): the library's PL-sphere test gives
+    the stored flags (4 spheres), and its isomorphism classes put seeded relabelings of each
+    class with that class and nowhere else."""
+    from conftest import load_n11_seeds
+    _, classes, _ = load_n11_seeds()
+    reps = [K for _, _, K in classes]
+    got, k = wpm.pl_spheres(11, 15, *_as_flat(reps))
+    assert list(got) == [s for _, s, _ in classes] and k == 4
+    rng = np.random.default_rng(15)
+    complexes, want = [], []
+    for c, K in enumerate(reps):
+        for _ in range(3):
+            perm = rng.permutation(15)
+            complexes.append([sum(1 << int(perm[u]) for u in range(15) if (F >> u) & 1)
+                              for F in K])
+            want.append(c)
+    order = rng.permutation(len(complexes))
+    cls, count = wpm.iso_classes(15, *_as_flat([complexes[i] for i in order]))
+    assert count == len(reps)
+    labels = {}
+    for i, c in zip(order, cls):
+        assert labels.setdefault(int(c), want[i]) == want[i]
