@@ -19,6 +19,9 @@
  *                         by Proposition 2.1 over Z.
  *   orc_enumerate_dfs     the ridge-driven search (the canonical tree below), recursive,
  *                         with plain byte arrays. It also reports node and probe counts.
+ *   orc_enumerate_sweep_fixed  the sweep with Section 4.4's initialization: forced-in /
+ *                         forced-out facets fix part of X through a column echelon form
+ *                         of the kernel basis; only the rest is swept.
  *   orc_n2_cycle_sets     n = 2 only: a WPM of dimension 1 is a set of vertex-disjoint
  *                         cycles of the candidate graph; counted by graph search.
  *
@@ -503,6 +506,125 @@ int orc_enumerate_sweep(int n, int m, int M, const uint16_t *facets, const orc_c
     incidence_free(&I);
     rc = sink_finish(&snk);
     if (st) { st->count = snk.count; st->nodes = 0; st->probes = 0; }
+    return rc;
+}
+
+/* ---------------------------------------------------------------------------------- */
+/* O2 with Section 4.4's initialization (Enumeration for n = 11, condition (X)). The   */
+/* forced-in facets I and forced-out facets J fix part of X before the sweep: the      */
+/* generators (the columns of B, here the kernel basis vectors) are brought to reduced */
+/* column echelon form with the rows taken in the order I, J, the rest. The columns    */
+/* whose leading row lies in I must have x_t = 1, those whose leading row lies in J    */
+/* x_t = 0, and the other columns are zero on every row of I and J, so only they are   */
+/* swept. If the fixed part already gives a row of I the value 0 or a row of J the     */
+/* value 1, no K satisfies the conditions. nodes reports the combinations swept.       */
+/* ---------------------------------------------------------------------------------- */
+
+int orc_enumerate_sweep_fixed(int n, int m, int M, const uint16_t *facets, const orc_cond *c,
+                              uint64_t *masks, uint64_t cap_masks, orc_stats *st, int max_free)
+{
+    int cap = resolve_cap(c->cap, n, m);
+    if (cap == -3) return ORC_ERR_INPUT;
+    incidence_t I;
+    int rc = incidence_build(n, M, facets, &I);
+    if (rc) return rc;
+    uint64_t *B = NULL;
+    int s = 0;
+    rc = gf2_kernel_basis(&I, &B, &s);
+    if (rc) { incidence_free(&I); return rc; }
+    int W = (M + 63) / 64;
+    /* the row order: I, then J, then the rest */
+    int *order = (int *)malloc(sizeof(int) * (M ? M : 1));
+    int n_i = 0, n_j = 0, k = 0;
+    for (int pass = 0; pass < 3; pass++)
+        for (int j = 0; j < M; j++) {
+            int in_i = c->forced_in && bit_of(c->forced_in, j);
+            int in_j = !in_i && c->forced_out && bit_of(c->forced_out, j);
+            int want = pass == 0 ? in_i : pass == 1 ? in_j : (!in_i && !in_j);
+            if (!want) continue;
+            order[k++] = j;
+            n_i += pass == 0;
+            n_j += pass == 1;
+        }
+    /* reduced column echelon form: one leading row per pivot column, in row order */
+    int *lead = (int *)malloc(sizeof(int) * (s ? s : 1));
+    int piv = 0;
+    for (int q = 0; q < M && piv < s; q++) {
+        int j = order[q];
+        int t = -1;
+        for (int u = piv; u < s; u++)
+            if (bit_of(B + (size_t)u * W, j)) { t = u; break; }
+        if (t < 0) continue;
+        if (t != piv)
+            for (int w = 0; w < W; w++) {
+                uint64_t x = B[(size_t)t * W + w];
+                B[(size_t)t * W + w] = B[(size_t)piv * W + w];
+                B[(size_t)piv * W + w] = x;
+            }
+        for (int u = 0; u < s; u++)
+            if (u != piv && bit_of(B + (size_t)u * W, j))
+                for (int w = 0; w < W; w++) B[(size_t)u * W + w] ^= B[(size_t)piv * W + w];
+        lead[piv++] = q;
+    }
+    int s_i = 0, s_j = 0;   /* pivot columns led by rows of I, and by rows of I or J */
+    for (int t = 0; t < piv; t++) {
+        if (lead[t] < n_i) s_i++;
+        if (lead[t] < n_i + n_j) s_j++;
+    }
+    int n_free = s - s_j;
+    if (n_free > max_free || n_free > 62) {
+        free(order); free(lead); free(B); incidence_free(&I);
+        return ORC_ERR_INPUT;
+    }
+    /* X fixed on its first s_J entries: x_t = 1 for t < s_I, 0 for s_I <= t < s_J */
+    char *inK = (char *)calloc(M ? M : 1, 1);
+    for (int t = 0; t < s_i; t++)
+        for (int j = 0; j < M; j++)
+            if (bit_of(B + (size_t)t * W, j)) inK[j] = (char)!inK[j];
+    int feasible = 1;
+    for (int q = 0; q < n_i + n_j; q++)
+        if (inK[order[q]] != (q < n_i)) feasible = 0;
+    int base = c->base_facet ? base_facet_index(n, M, facets) : -1;
+    sink_t snk = { masks, cap_masks, 0, W, 0 };
+    uint64_t swept = 0;
+    if (feasible) {
+        int *deg = (int *)calloc(I.N ? I.N : 1, sizeof(int));
+        int bad = 0, size = 0;
+        for (int j = 0; j < M; j++) {
+            if (!inK[j]) continue;
+            size++;
+            for (int kk = 0; kk < n; kk++) deg[I.fr[j * n + kk]]++;
+        }
+        for (int r = 0; r < I.N; r++) bad += !(deg[r] == 0 || deg[r] == 2);
+        for (uint64_t i = 0; i < (1ull << n_free); i++) {
+            if (i > 0) {   /* Gray order over the free columns s_J .. s-1 */
+                int t = s_j + __builtin_ctzll(i);
+                for (int j = 0; j < M; j++) {
+                    if (!bit_of(B + (size_t)t * W, j)) continue;
+                    int delta = inK[j] ? -1 : 1;
+                    inK[j] = (char)!inK[j];
+                    size += delta;
+                    for (int kk = 0; kk < n; kk++) {
+                        int r = I.fr[j * n + kk];
+                        int before_ok = (deg[r] == 0 || deg[r] == 2);
+                        deg[r] += delta;
+                        int after_ok = (deg[r] == 0 || deg[r] == 2);
+                        bad += before_ok - after_ok;
+                    }
+                }
+            }
+            swept++;
+            if (bad) continue;
+            if (cap >= 0 && size > cap) continue;
+            if (c->base_facet && (base < 0 || !inK[base])) continue;
+            if (affine_ok(c, M, inK)) sink_emit(&snk, M, inK);
+        }
+        free(deg);
+    }
+    free(inK); free(order); free(lead); free(B);
+    incidence_free(&I);
+    rc = sink_finish(&snk);
+    if (st) { st->count = snk.count; st->nodes = swept; st->probes = (uint64_t)n_free; }
     return rc;
 }
 

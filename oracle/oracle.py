@@ -64,6 +64,9 @@ def lib():
                                              u64p, C.c_uint64, C.POINTER(_Stats)]
             L.orc_enumerate_sweep.argtypes = [C.c_int, C.c_int, C.c_int, u16p, C.POINTER(_Cond),
                                               u64p, C.c_uint64, C.POINTER(_Stats), C.c_int]
+            L.orc_enumerate_sweep_fixed.argtypes = [C.c_int, C.c_int, C.c_int, u16p,
+                                                    C.POINTER(_Cond), u64p, C.c_uint64,
+                                                    C.POINTER(_Stats), C.c_int]
             L.orc_enumerate_dfs_budget.argtypes = [C.c_int, C.c_int, C.c_int, u16p,
                                                    C.POINTER(_Cond), C.POINTER(_Stats),
                                                    C.c_uint64]
@@ -197,6 +200,17 @@ def enumerate_sweep(n, m, facets, cap=CAP_NONE, base_facet=False, forced_in=None
     """O2: sweep of ker_Z2 A (Section 2.1)."""
     return _enumerate(lib().orc_enumerate_sweep, n, m, facets, cap, base_facet, forced_in,
                       forced_out, affine, list_mode, capacity, extra=(max_s,))
+
+
+def enumerate_sweep_fixed(n, m, facets, cap=CAP_NONE, base_facet=False, forced_in=None,
+                          forced_out=None, affine=None, list_mode=True, capacity=1 << 12,
+                          max_free=30):
+    """O2 with Section 4.4's initialization: forced-in / forced-out facets fix part of the
+    kernel coordinates X (column echelon form of the kernel basis, rows in the order I, J,
+    rest); only the free coordinates are swept. Returns (count, combinations swept, number
+    of free coordinates, masks)."""
+    return _enumerate(lib().orc_enumerate_sweep_fixed, n, m, facets, cap, base_facet,
+                      forced_in, forced_out, affine, list_mode, capacity, extra=(max_free,))
 
 
 def n2_cycle_sets(edges: np.ndarray, max_edges: int = -1) -> int:

@@ -7,7 +7,9 @@ what they find. Checked here against
     n = 10 count at line 7, for the stored results of make_n11_seeds.py;
   - the definition of the conditions: a conditioned search returns exactly the WPMs of the
     unconditioned search whose apex link is L (on small maps, every link of every output);
-  - invariants of every stored class and sample (seedness, PL sphereness, the apex link).
+  - invariants of every stored class and sample (seedness, PL sphereness, the apex link);
+  - the paper's own initialization for these runs (the kernel sweep with the leading
+    coordinates fixed by a column echelon form), which must give the same WPMs.
 """
 import numpy as np
 import pytest
@@ -79,6 +81,23 @@ def test_sample_link_conditions_and_search(idx):
         assert _apex_link(K, APEX) == sorted(L)
 
 
+@pytest.mark.parametrize("idx", range(len(SAMPLES)))
+def test_sample_links_by_the_papers_initialization(idx):
+    """Section 4.4's own route: conditions (1), (2) fix the leading coordinates of X in a
+    column echelon form of the kernel basis and only the rest is swept; same WPMs as the
+    conditioned search."""
+    orbit, words, count = SAMPLES[idx][:3]
+    rep, L = _link(orbit, words)
+    _, f, fin, fout = O.link_conditions(N, M, rep, L)
+    c, swept, n_free, masks = O.enumerate_sweep_fixed(N, M, f, cap=O.CAP_UBT, forced_in=fin,
+                                                      forced_out=fout, capacity=64)
+    c2, _, _, masks2 = O.enumerate_dfs(N, M, f, cap=O.CAP_UBT, forced_in=fin,
+                                       forced_out=fout, capacity=64)
+    assert c == c2 == count
+    assert np.array_equal(masks, masks2)
+    assert n_free < O.kernel_dim(N, f) == 64 and swept == 1 << n_free
+
+
 @pytest.mark.parametrize("seed", [0, 1, 2])
 def test_conditioned_search_is_the_definition(seed):
     """Picard number 3, n = 4, m = 7 = 2^3 - 1 (the apex row is then fixed by mu, as for
@@ -102,6 +121,29 @@ def test_conditioned_search_is_the_definition(seed):
                                            list_mode=True, capacity=1 << 12)
         got = {tuple(sorted(O.masks_to_facets(f2, masks2[i]))) for i in range(c2)}
         assert got == groups[L]
+        c3, _, _, masks3 = O.enumerate_sweep_fixed(n, m, f2, forced_in=fin, forced_out=fout,
+                                                   capacity=1 << 12)
+        assert c3 == c2 and np.array_equal(masks3, masks2)
+
+
+def test_papers_initialization_with_unsatisfiable_conditions():
+    """Forced sets that no WPM meets (a facet forced in with every other parent of one of
+    its ridges forced out): the fixed sweep finds nothing, as the search does."""
+    n, m = 4, 7
+    rows = I.SplitMix64(5).shuffle(list(range(1, 8)))
+    f = O.candidate_facets("dual", n, m, rows)
+    W = (len(f) + 63) // 64
+    a = 0
+    r = int(f[a]) & ~(int(f[a]) & -int(f[a]))          # a ridge of facet 0
+    fin = np.zeros(W, dtype=np.uint64)
+    fout = np.zeros(W, dtype=np.uint64)
+    fin[0] |= np.uint64(1)
+    for j, s in enumerate(f):
+        if j != a and (int(s) & r) == r:
+            fout[j // 64] |= np.uint64(1 << (j % 64))
+    c, _, _, _ = O.enumerate_sweep_fixed(n, m, f, forced_in=fin, forced_out=fout)
+    c2, _, _, _ = O.enumerate_dfs(n, m, f, forced_in=fin, forced_out=fout)
+    assert c == c2 == 0
 
 
 def test_conditioned_search_brute_force_pic4_n2():
