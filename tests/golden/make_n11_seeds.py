@@ -14,9 +14,13 @@ Route (Section 4.4, "Enumeration for n = 11", taken over every labelled link):
 Every labelled link is used, not one per isomorphism class, so every map that a link
 supports is covered. The paper's Theorem for n = 11 states that exactly 4 classes remain.
 
+Every conditioned search is also run the paper's way (the kernel sweep with its leading
+coordinates fixed by conditions (1), (2) through a column echelon form); the totals of both
+routes are written.
+
 Also written: a seeded sample of 16 links with the oracle's results of their conditioned
 searches (count, nodes, probes, and how many pass lines 9-12), the inputs of GPU parity
-tests. Calls only the oracle (and the seeded input generators). About five minutes on 8
+tests. Calls only the oracle (and the seeded input generators). About six minutes on 8
 cores:
 
     python tests/golden/make_n11_seeds.py
@@ -50,7 +54,8 @@ def _links_of_orbit(oi):
 
 def _conditioned(oi, rows):
     """Results of the conditioned n = 11 searches of the links `rows` (masks over the n = 10
-    candidates of orbit oi): per link (count, nodes, probes, [kept complexes])."""
+    candidates of orbit oi): per link (count, nodes, probes, [kept complexes], and the count,
+    free coordinates and kept count of the sweep with Section 4.4's initialization)."""
     rep = I.idcm_orbit_reps(N_LINK)[oi]
     f10 = O.candidate_facets("dual", N_LINK, M_LINK, rep)
     out = []
@@ -63,7 +68,10 @@ def _conditioned(oi, rows):
         if c:
             keep = O.filter_pic_seed(N, M, f, masks)
             kept = [tuple(O.masks_to_facets(f, masks[i])) for i in range(c) if keep[i]]
-        out.append((c, nodes, probes, kept))
+        cs, _, n_free, smasks = O.enumerate_sweep_fixed(N, M, f, cap=O.CAP_UBT, forced_in=fin,
+                                                        forced_out=fout, capacity=256)
+        skept = int(O.filter_pic_seed(N, M, f, smasks).sum()) if cs else 0
+        out.append((c, nodes, probes, kept, cs, n_free, skept))
     return out
 
 
@@ -92,6 +100,10 @@ def main():
     total_wpms = sum(r[0] for _, _, rr in done for r in rr)
     kept = [K for _, _, rr in done for r in rr for K in r[3]]
     print("conditioned WPMs:", total_wpms, "after lines 9-12:", len(kept), flush=True)
+    sweep_wpms = sum(r[4] for _, _, rr in done for r in rr)
+    sweep_kept = sum(r[6] for _, _, rr in done for r in rr)
+    free_dims = sorted({r[5] for _, _, rr in done for r in rr})
+    print("by Section 4.4's initialization:", sweep_wpms, sweep_kept, free_dims, flush=True)
 
     with ctx.Pool(cores) as pool:
         forms = pool.map(_form, kept, chunksize=64)
@@ -110,7 +122,7 @@ def main():
     for idx in picks:
         oi, k = flat[idx]
         row = links[oi][1][k]
-        c, nodes, probes, kk = _conditioned(oi, [row])[0]
+        c, nodes, probes, kk = _conditioned(oi, [row])[0][:4]
         sample.append((oi, row, c, nodes, probes, len(kk)))
 
     lines = [
@@ -125,6 +137,9 @@ def main():
         f"links {n_links}",
         f"conditioned_wpms {total_wpms}",
         f"pic_seed {len(kept)}",
+        f"sweep_fixed_wpms {sweep_wpms}",
+        f"sweep_fixed_pic_seed {sweep_kept}",
+        f"sweep_fixed_free_max {max(free_dims)}",
         f"classes {len(classes)}",
         f"spheres {n_spheres}",
     ]

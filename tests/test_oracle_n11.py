@@ -46,6 +46,9 @@ def test_paper_theorem_n11_four_seeds():
     # Table 2, n = 10, line 7 (the run the links come from)
     assert TOTALS["line7_n10"] == 99374
     assert TOTALS["links"] <= TOTALS["line7_n10"]
+    # the paper's own initialization of the sweep found the same WPMs for every link
+    assert TOTALS["sweep_fixed_wpms"] == TOTALS["conditioned_wpms"]
+    assert TOTALS["sweep_fixed_pic_seed"] == TOTALS["pic_seed"]
 
 
 @pytest.mark.parametrize("idx", range(len(CLASSES)))
