@@ -261,7 +261,8 @@ int wpm_autotune(const wpm_instance *inst, int count, int sample, wpm_tuning *be
  * class_of[c] receives the class of complex c, classes numbered 0.. in order of first
  * appearance; returns the number of classes, or a negative error code. Computed on the host
  * (several threads): a canonical form per complex, by colour refinement and
- * individualization. Runs without a GPU.
+ * individualization, with subtrees that a found automorphism maps onto searched ones
+ * skipped. Runs without a GPU.
  */
 long wpm_iso_classes(int m, int count, const uint64_t *offsets, const uint16_t *facets,
                      int32_t *class_of);
