@@ -17,6 +17,9 @@ native host code. This module only hands each call's output to the next.
                               conditioned searches.
   colorable_seeds_n11()       the paper's n = 11 run: the 114 PL spheres of n = 10 (seeds
                               and non-seeds) as links, one map each, then seeds_from_links.
+  main_theorem_p4()           the main theorem's Picard-4 row: line 19 for n = 2..10, plus
+                              the 4-cross-polytope that Section 4.3 adds at n = 4
+                              (extra_n4_seed checks it), plus the n = 11 seeds.
 """
 from __future__ import annotations
 
