@@ -60,29 +60,55 @@ TDFS_DRAM_BYTES_PER_NODE = 410.7e6 / 2711713518
 # ------------------------------------------------------------------------------------------
 
 def _oracle_job(args):
-    kind, n, m, cols = args
+    k, kind, n, m, cols, keep = args
     import oracle as O
     f = O.candidate_facets(kind, n, m, cols)
-    c, nodes, probes, _ = O.enumerate_dfs(n, m, f, cap=O.CAP_UBT, list_mode=True, capacity=1 << 16)
-    return c, nodes, probes
+    # room for every list of this workload (the oracle searches again when a list overflows)
+    c, nodes, probes, masks = O.enumerate_dfs(n, m, f, cap=O.CAP_UBT, list_mode=True,
+                                              capacity=1 << 20)
+    return k, c, nodes, probes, (masks if keep else None)
 
 
 def oracle_sample(insts, stride):
-    """Every stride-th instance of the batch (a bounded, deterministic sample)."""
-    return [i for k, i in enumerate(insts) if k % stride == 0]
+    """Every stride-th instance of the batch (a bounded, deterministic sample), with its
+    index in the batch."""
+    return [(k, i) for k, i in enumerate(insts) if k % stride == 0]
 
 
-def time_oracle(sample, cores):
+def time_oracle(sample, cores, keep=False):
+    """The oracle over the sample in a spawn pool: (nodes, seconds, {index: (count, nodes,
+    probes, sorted masks or None)})."""
     import oracle as O
     O.oracle.build()
     ctx = mp.get_context("spawn")
     # longest first (the search grows about 5x per unit of n), so the pool stays busy
-    jobs = sorted(((i.kind, i.n, i.m, list(i.cols)) for i in sample), key=lambda j: -j[1])
+    jobs = sorted(((k, i.kind, i.n, i.m, list(i.cols), keep) for k, i in sample),
+                  key=lambda j: -j[2])
     t0 = time.perf_counter()
     with ctx.Pool(cores) as pool:
         res = list(pool.imap_unordered(_oracle_job, jobs, chunksize=1))
     dt = time.perf_counter() - t0
-    return sum(r[1] for r in res), dt, res
+    return sum(r[2] for r in res), dt, {r[0]: r[1:] for r in res}
+
+
+def parity_sample(oracle_res, out, dev_out, words):
+    """The timed run's last step against the oracle on the sampled maps: per map the count,
+    node and probe counts, and the sorted mask list read back from the device buffers."""
+    import numpy as np
+    bad = []
+    for k, (c, nodes, probes, masks) in sorted(oracle_res.items()):
+        r = out[k]
+        if (r.status, r.count, r.nodes, r.probes) != (0, c, nodes, probes):
+            bad.append({"map": k, "gpu": [r.status, r.count, r.nodes, r.probes],
+                        "oracle": [0, c, nodes, probes]})
+            continue
+        w = words[k]
+        got = dev_out[k][: c * w].cpu().numpy().view(np.uint64).reshape(c, w)
+        if not np.array_equal(got, masks):
+            bad.append({"map": k, "masks_differ": True})
+    return {"maps": len(oracle_res), "exact": not bad, "mismatches": bad[:8],
+            "compared": "status, count, nodes, probes and the sorted mask list of each "
+                        "sampled map (every stride-th of the batch), from the last timed step"}
 
 
 # ------------------------------------------------------------------------------------------
@@ -320,7 +346,7 @@ def reduce_over_ranks(ms, nodes, launches, world, device):
     return float(mx[0]), float(sm[1]), float(sm[2])
 
 
-def run_ours(args, rank, world):
+def run_ours(args, rank, world, oracle_res=None):
     import numpy as np
     import torch
     from paper_2301_00806_gb300 import instances as I, wpm
@@ -386,6 +412,7 @@ def run_ours(args, rank, world):
     ms = ev0.elapsed_time(ev1)
     assert all(r.status == 0 for r in out)
     assert sum(r.nodes for r in out) == nodes_step
+    parity = parity_sample(oracle_res, out, dev_out, words) if oracle_res else None
 
     # end to end through the C ABI with host buffers (inputs in, sorted lists out)
     host_caps = caps
@@ -457,6 +484,7 @@ def run_ours(args, rank, world):
                      "peak_from": f"{n_sm} SMs x 128 INT32 lanes x {peak_mhz:.0f} MHz (max clock)"},
         "gpu_launches": launches,
         "clocks": clocks,
+        "parity_sample": parity,
     }
     if world == 1 and args.table1:
         line["plain_configs"] = run_plain_configs(stream)
@@ -533,17 +561,20 @@ def main():
 
     # CPU baseline first (spawn pool, before any CUDA call), rank 0 at N=1 only
     cpu = None
+    oracle_res = None
     if rank == 0 and world == 1 and args.cpu_stride > 0:
         insts = I.batch_duals(args.count, 3, 8, seed=args.seed)
         sample = oracle_sample(insts, args.cpu_stride)
-        nodes, dt, _ = time_oracle(sample, cores)
+        nodes, dt, oracle_res = time_oracle(sample, cores, keep=True)
         cpu = {"value": nodes / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"every {args.cpu_stride}th of the {args.count} instances "
                          f"({len(sample)} maps, {nodes} nodes, {dt:.1f} s)"}
-    line = run_ours(args, rank, world)
+    line = run_ours(args, rank, world, oracle_res)
     if line is not None:
         line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
+        if line.get("parity_sample") and not line["parity_sample"]["exact"]:
+            sys.exit("parity_sample: the GPU run differs from the oracle on sampled maps")
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

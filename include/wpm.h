@@ -122,6 +122,8 @@ typedef struct {
     int32_t N;               /* out: ridges                                                */
     int32_t status;          /* out: this instance's WPM_* code (batched calls)            */
     int32_t reserved;
+    uint64_t found;          /* out: WPMs the search found, before any post-filter (equals
+                                count when wpm_conditions.post_filter is 0)                 */
 } wpm_output;
 
 /* One instance of a batch. Pointers are host pointers, read during the call only. */
@@ -177,7 +179,17 @@ typedef struct {
                                1024 and s <= sweep_max_s, else WPM_ERR_LIMIT. Same counts and
                                lists; `nodes` then counts kernel elements visited, `probes` 0 */
     int32_t sweep_max_s;    /* largest kernel dimension the sweep accepts (0 = 30, max 48)  */
-    int32_t reserved[2];
+    /* Bounds of the per-thread passes' device waits (they only end waits that end by
+       themselves in a correct run). ready_polls: polls of a work item's ready flag before the
+       reader gives up; the kernel then returns and the run fails with WPM_ERR_TIMEOUT (0 =
+       2^22, about half a second). idle_polls: fruitless steps after which a search waiting
+       for work leaves the pass (0 = 2^14); leaving early never changes counts.           */
+    int32_t ready_polls;
+    int32_t idle_polls;
+    int32_t test_unpublished; /* test hook, 0 in normal use: nonzero makes readers of items
+                               written during a pass wait for a ready stamp that no writer
+                               raises, so every such wait runs out (WPM_ERR_TIMEOUT)        */
+    int32_t reserved;
 } wpm_tuning;
 
 /* Statistics of the calling thread's last enumeration run. */
@@ -305,14 +317,15 @@ int wpm_link_conditions(int n, int m, const uint32_t *mu_rows, uint32_t apex_row
 
 /*
  * wpm_candidate_facets with no allocation (the paper has no counterpart: this serves callers
- * that must not allocate, e.g. a service that reserved its device memory at start-up, a host
- * framework whose allocator owns the device, or code running while a stream is captured into
- * a CUDA graph). Same inputs and output as wpm_candidate_facets (host pointers), run on
- * `cuda_stream` (NULL: the default stream), which the call synchronises. Its device scratch
- * is one fixed 512 KiB __device__ array of the library, present on every GPU that loads
- * it; maps with C(m,n) + C(m,n-1) beyond about 7000 ranks are rejected with WPM_ERR_LIMIT.
- * The first call on a device looks up that array's address (make it before any stream
- * capture). Calls share the array: calls that overlap on the GPU race.
+ * that must not allocate, e.g. a service that reserved its device memory at start-up, or a
+ * host framework whose allocator owns the device). Same inputs and output as
+ * wpm_candidate_facets (host pointers), run on `cuda_stream` (NULL: the default stream),
+ * which the call synchronises before it returns. Its device scratch is one fixed 512 KiB
+ * __device__ array of the library, present on every GPU that loads it; a map needs about
+ * 38 C(m,n) + 36 C(m,n-1) bytes of it (n = 6 on 16 vertices fits, n = 7 on 16 does not), and
+ * larger maps are rejected with WPM_ERR_LIMIT. The first call on a device looks up that
+ * array's address (make it before any stream capture). Calls share the array: calls that
+ * overlap on the GPU race.
  */
 int wpm_candidate_facets_static(const uint32_t *lambda_cols, int kind, int n, int m,
                                 uint16_t *facets_out, int cap, void *cuda_stream);
@@ -340,7 +353,9 @@ typedef struct {
 /* Create an engine on the current device; stream may be NULL (the engine's own stream). */
 int wpm_engine_create(const wpm_engine_config *cfg, void *cuda_stream, wpm_engine **out);
 /* Queue a job (copied; pointers may be freed after the call). mode as above;
- * out_capacity: masks to reserve in list mode. job_id receives a handle. */
+ * out_capacity: masks to reserve in list mode. job_id receives a handle. A list-mode job
+ * whose output region (2 * 8 * ceil(C(m,n)/64) * out_capacity bytes) exceeds the engine's
+ * memory_bytes is refused with WPM_ERR_NOMEM (it could never be admitted). */
 int wpm_engine_submit(wpm_engine *e, const wpm_instance *inst, int mode,
                       uint64_t out_capacity, uint64_t *job_id);
 /* Admit what fits, run one search pass over everything resident, retire finished jobs.

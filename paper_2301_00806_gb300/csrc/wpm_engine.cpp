@@ -319,7 +319,8 @@ int pass(wpm_engine *e) {
   CUDA_TRY(cudaStreamSynchronize(e->s));
   if (hq->err & 1ull) return fail(WPM_ERR_NOMEM, "engine work ring overflow");
   if (hq->err & 2ull) return fail(WPM_ERR_LIMIT, "engine search stack overflow");
-  if (hq->err & 4ull) return fail(WPM_ERR_CUDA, "engine: a work item was never published");
+  if (hq->err & 4ull)
+    return fail(WPM_ERR_TIMEOUT, "engine: a work item was not published within the bounded wait");
   e->head = std::min(hq->head, hq->tail);  // items written during the pass are taken too
   e->tail = hq->tail;
   e->parked = hq->parked;
@@ -479,6 +480,15 @@ int wpm_engine_submit(wpm_engine *e, const wpm_instance *inst, int mode, uint64_
   if (rc == WPM_OK) rc = copy_conditions(inst->cond, j->hi);
   if (rc == WPM_OK && j->hi.post)
     rc = fail(WPM_ERR_INPUT, "engine: post filters are applied by wpm_enumerate_batch only");
+  if (rc == WPM_OK && mode == WPM_MODE_LIST) {
+    // a job whose output region exceeds the engine's whole output memory could never be
+    // admitted (and would hold up every job behind it): refuse it now
+    const size_t words = (binom_e(j->hi.m, j->hi.n) + 63) / 64;
+    const size_t bytes = a256(2 * 8 * words * std::max<uint64_t>(out_capacity, 1));
+    if (bytes > e->pool_bytes)
+      rc = fail(WPM_ERR_NOMEM, "engine: the job's output region (%zu bytes) exceeds the "
+                "engine's output memory (%zu bytes)", bytes, e->pool_bytes);
+  }
   if (rc != WPM_OK) {
     delete j;
     return rc;
@@ -539,6 +549,7 @@ int wpm_engine_result(wpm_engine *e, uint64_t job_id, wpm_output *out) {
                                                             (unsigned long long)job_id);
   Job *j = it->second;
   out->count = j->count;
+  out->found = j->count;  // the engine applies no post-filters
   out->nodes = j->nodes;
   out->probes = j->probes;
   out->words_per_mask = j->ow;

@@ -96,7 +96,7 @@ struct QueueCtl {
   unsigned long long epoch;       // per-thread passes: the pass's ready-flag stamp (1, 2, ...)
   unsigned long long passes;      // depth-first passes run by a graph-driven loop
   alignas(128) unsigned long long err;  // nonzero: 1 ring overflow, 2 stack overflow, 4 an
-                                        // item never published
+                                        // item not published within the bounded wait
   unsigned long long idle;        // per-warp passes: searches of this pass that have stopped
   unsigned long long nodes;       // nodes searched in this pass (tracing)
   unsigned long long parked;      // searches that parked their work at the end of this pass
@@ -150,7 +150,17 @@ struct PassArgs {
   int donate_every;               // nodes a search searches between two hand-overs
   unsigned long long time_left_ns;  // > 0: searches leave the pass (parking their work) this
                                     // long after it started
+  int ready_polls;                // polls of a ready flag before the item is reported lost
+                                  // (0: kDefaultReadyPolls)
+  int idle_polls;                 // fruitless steps before a waiting search leaves the pass
+                                  // (0: kDefaultIdlePolls)
+  uint32_t ready_xor;             // test hook: readers wait for epoch ^ ready_xor (0 in use)
+  int pad2;
 };
+
+// Defaults of PassArgs::ready_polls / idle_polls.
+constexpr int kDefaultReadyPolls = 1 << 22;
+constexpr int kDefaultIdlePolls = 1 << 14;
 
 // Park record header words (before the item words of the parked node).
 constexpr int kParkHeader = 4;  // valid, top entry, depth | base << 16, unused
@@ -234,6 +244,8 @@ cudaError_t launch_sort_pass(const InstDesc *d_inst, const OutDesc *d_outs, cons
 
 // Record the calling thread's last error (wpm_last_error) and return `code`.
 int set_last_error(int code, const char *msg);
+// Forget the calling thread's last error (every entry point does this first).
+void clear_last_error();
 
 // Copy segment s: prefix[s+1] - prefix[s] words from src to dst (device pointers).
 struct CopySeg {

@@ -3,12 +3,12 @@
 //
 // Some callers cannot let a library call cudaMalloc: a service that reserves its device
 // memory once at start-up and must never grow it under load (an allocation can fail, or wait
-// on other users of the GPU), a host framework whose allocator owns all device memory, and
-// code that runs while a stream is being captured into a CUDA graph, where cudaMalloc is not
-// allowed. This entry point runs the same setup kernel as wpm_candidate_facets, but its
-// scratch (the instance descriptor, the rank prefix sums and the incidence rows the kernel
-// builds) lives in one file-scope __device__ array below, and its host side uses only stack
-// variables.
+// on other users of the GPU), or a host framework whose allocator owns all device memory.
+// This entry point runs the same setup kernel as wpm_candidate_facets, but its scratch (the
+// instance descriptor, the rank prefix sums and the incidence rows the kernel builds) lives
+// in one file-scope __device__ array below, and its host side uses only stack variables.
+//
+// The call copies its result back to the host and synchronises its stream before it returns.
 //
 // Every GPU that loads the library holds that array (kStaticScratchBytes) until the process
 // exits. All calls share it and it keeps the last call's contents; the kernel writes every
@@ -26,9 +26,11 @@
 
 namespace wpm {
 
-// Room for one instance's descriptor and setup tables: 512 KiB covers every Picard-4 map
-// (the largest, n = 11 on 15 vertices, needs about 170 KB) and any map with
-// C(m, n) + C(m, n - 1) up to about 7000 lexicographic ranks.
+// Room for one instance's descriptor and setup tables. A map needs, rounded up to 256 bytes
+// per table, 38 bytes per facet rank and 36 per ridge rank: about 38 C(m,n) + 36 C(m,n-1)
+// bytes plus 1.5 KB. 512 KiB covers every Picard-4 map (the largest, n = 11 on 15 vertices,
+// needs about 170 KB) and, for example, n = 6 on 16 vertices (about 463 KB, 12,376 ranks);
+// n = 7 on 16 vertices (about 725 KB) is rejected.
 constexpr size_t kStaticScratchBytes = 512u * 1024u;
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
@@ -54,6 +56,7 @@ using namespace wpm;
 extern "C" int wpm_candidate_facets_static(const uint32_t *lambda_cols, int kind, int n, int m,
                                            uint16_t *facets_out, int cap, void *cuda_stream) {
   std::lock_guard<std::mutex> g(g_static_mu);
+  clear_last_error();
   if (kind != WPM_LAMBDA_PRIMAL && kind != WPM_LAMBDA_DUAL)
     return set_last_error(WPM_ERR_INPUT, "kind is neither primal nor dual");
   if (n < 2 || m <= n || m > WPM_MAX_VERTICES)

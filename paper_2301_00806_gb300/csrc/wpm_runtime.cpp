@@ -45,6 +45,8 @@ int fail(int code, const char *fmt, ...) {
 
 int set_last_error(int code, const char *msg) { return fail(code, "%s", msg); }
 
+void clear_last_error() { t_err.clear(); }
+
 // Device buffers reused across calls on one device.
 // The depth-first pass loop as an instantiated CUDA graph: a conditional while node whose
 // body is prep, the pass and check. Kept while the pass's arguments stay the same.
@@ -196,6 +198,7 @@ int copy_facet_list(const uint16_t *facets, int M, int n, int m, HostInst &h) {
 struct InstResult {
   int status = WPM_OK;
   unsigned long long count = 0, nodes = 0, probes = 0;
+  unsigned long long found = 0;  // count before the post-filters
   int M = 0, N = 0, ow = 1;
 };
 
@@ -215,6 +218,9 @@ struct RunOptions {
   int engine = 0;  // 1: GF(2) cycle-space sweep
   int sweep_max_s = 0;
   long long hungry_items = 0;
+  int ready_polls = 0;
+  int idle_polls = 0;
+  int test_unpublished = 0;
   bool profile = false;
   bool setup_only = false;  // stop after the setup kernel (candidate facets)
 };
@@ -612,6 +618,9 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
     pa.feed = opt.feed_levels > 0 ? opt.feed_levels : (opt.feed_levels < 0 ? (1 << 20) : 8);
     pa.donate = opt.donate_levels > 0 ? opt.donate_levels : (opt.donate_levels < 0 ? 0 : 4);
     pa.donate_every = opt.donate_every > 0 ? opt.donate_every : 2048;
+    pa.ready_polls = opt.ready_polls;
+    pa.idle_polls = opt.idle_polls;
+    pa.ready_xor = opt.test_unpublished ? 0x80000000u : 0u;
     const int idle_pct = (opt.idle_percent > 0 && opt.idle_percent <= 100) ? opt.idle_percent : 20;
     pa.idle_limit = std::max<unsigned long long>(1, (unsigned long long)n_searches * idle_pct / 100);
     const bool trace = getenv("WPM_TRACE") != nullptr;
@@ -698,7 +707,8 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
         CUDA_TRY(cudaStreamSynchronize(s));
         if (hq->err & 1ull) return fail(WPM_ERR_NOMEM, "work ring overflow (raise ring_items)");
         if (hq->err & 2ull) return fail(WPM_ERR_LIMIT, "search stack overflow");
-        if (hq->err & 4ull) return fail(WPM_ERR_CUDA, "a work item was never published");
+        if (hq->err & 4ull)
+          return fail(WPM_ERR_TIMEOUT, "a work item was not published within the bounded wait");
         if (hq->err & 8ull) return fail(WPM_ERR_CUDA, "pass loop did not finish");
         t_stats.dfs_passes += hq->passes;
         t_stats.kernel_launches += 3 * hq->passes;
@@ -747,7 +757,8 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
       CUDA_TRY(cudaStreamSynchronize(s));
       if (hq->err & 1ull) return fail(WPM_ERR_NOMEM, "work ring overflow (raise ring_items)");
       if (hq->err & 2ull) return fail(WPM_ERR_LIMIT, "search stack overflow");
-      if (hq->err & 4ull) return fail(WPM_ERR_CUDA, "a work item was never published");
+      if (hq->err & 4ull)
+        return fail(WPM_ERR_TIMEOUT, "a work item was not published within the bounded wait");
       // per-thread passes also take items written during the pass (their head never passes
       // the tail); per-warp passes take only items that were there when it began
       const unsigned long long taken_to =
@@ -787,6 +798,7 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
     InstResult &r = res[i];
     const unsigned long long *c = hc2 + kCtrN * i;
     r.count = c[kCtrCount];
+    r.found = r.count;
     r.nodes = c[kCtrNodes];
     r.probes = c[kCtrProbes];
     if (timed_out && c[kCtrLive] != 0) {  // items of this instance are still in the ring
@@ -930,6 +942,7 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
 
 static void fill_output(const InstResult &r, wpm_output *o) {
   o->count = r.count;
+  o->found = r.found;
   o->nodes = r.nodes;
   o->probes = r.probes;
   o->words_per_mask = r.ow;
@@ -957,6 +970,9 @@ static RunOptions options_from(const wpm_tuning *t, int mode) {
     o.engine = t->engine;
     o.sweep_max_s = t->sweep_max_s;
     o.hungry_items = t->hungry_items;
+    o.ready_polls = t->ready_polls;
+    o.idle_polls = t->idle_polls;
+    o.test_unpublished = t->test_unpublished;
   }
   return o;
 }

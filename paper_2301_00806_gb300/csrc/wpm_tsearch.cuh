@@ -505,12 +505,11 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// Steps of a waiting search before it leaves the pass (a step takes on the order of a
-// microsecond), and polls of a ready flag before the item is reported lost. Both only bound
-// waits that end by themselves in a correct run; a search that leaves early only lowers the
+// PassArgs::idle_polls bounds the steps of a waiting search before it leaves the pass (a
+// step takes on the order of a microsecond), PassArgs::ready_polls the polls of a ready flag
+// before the item is reported lost (error 4, and the search goes on). Both only bound waits
+// that end by themselves in a correct run; a search that leaves early only lowers the
 // parallelism of the rest of the pass.
-constexpr int kMaxIdlePolls = 1 << 14;
-constexpr int kMaxReadyPolls = 1 << 22;
 
 template <class K>
 __global__ void __maxnreg__(96) tdfs_kernel(PassArgs a) {
@@ -527,6 +526,9 @@ __global__ void __maxnreg__(96) tdfs_kernel(PassArgs a) {
   // items there when the pass began (complete); later ones carry a ready flag
   const unsigned long long limit = q->limit;
   S.epoch = (uint32_t)q->epoch;
+  const uint32_t want_stamp = S.epoch ^ a.ready_xor;
+  const int max_ready = a.ready_polls > 0 ? a.ready_polls : kDefaultReadyPolls;
+  const int max_idle = a.idle_polls > 0 ? a.idle_polls : kDefaultIdlePolls;
   // Levels 1..depth of the stack are open (entry L at stk[(L - 1) * stride], the top one in
   // `top`); levels 1..base were given away, so the item is finished when the search pops
   // back to level base.
@@ -628,7 +630,7 @@ __global__ void __maxnreg__(96) tdfs_kernel(PassArgs a) {
           counted = false;
           continue;
         }
-        if (++polls >= kMaxIdlePolls || (vload(&q->full) && vload(&q->head) >= vload(&q->tail))) {
+        if (++polls >= max_idle || (vload(&q->full) && vload(&q->head) >= vload(&q->tail))) {
           atomicAdd(&q->waiting, (unsigned long long)-1ll);
           waiting = false;
           stop = true;
@@ -643,9 +645,9 @@ __global__ void __maxnreg__(96) tdfs_kernel(PassArgs a) {
       if (idx >= limit) {  // written during this pass: wait until it is complete
         const uint32_t *rf = a.ready + idx % a.ring_cap;
         int spins = 0;
-        while (*(const volatile uint32_t *)rf != S.epoch && ++spins < kMaxReadyPolls)
+        while (*(const volatile uint32_t *)rf != want_stamp && ++spins < max_ready)
           __nanosleep(32);
-        if (spins >= kMaxReadyPolls) {
+        if (spins >= max_ready) {
           atomicOr(&q->err, 4ull);
           continue;
         }

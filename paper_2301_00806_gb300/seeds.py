@@ -83,20 +83,23 @@ def _classes_and_spheres(n: int, m: int, found: _Found):
                      for c, K, s in zip(first, reps, is_sphere) if s]
 
 
-def _search(specs: List[wpm.BatchSpec], post: int, stream=None):
-    """Counting run (line 7) then list run with the post-filters; returns (line-7 count,
-    nodes, the complexes that pass)."""
+def _search(specs: List[wpm.BatchSpec], post: int, stream=None, capacity: int = 1 << 15):
+    """One list run with the post-filters (line 7, then lines 9-12 on the GPU); maps whose
+    WPMs overflow `capacity` are run again with room for exactly their count. Returns
+    (line-7 count, nodes, the complexes that pass)."""
     if not specs:
         return 0, 0, _Found()
-    counted = wpm.enumerate_batch(specs, list_mode=False, stream=stream)
-    for r in counted:
-        if r.status != wpm.OK:
-            raise wpm.WpmError(r.status, "counting run failed")
     listed_specs = [wpm.BatchSpec(s.kind, s.n, s.m, s.cols, cap=s.cap, base_facet=s.base_facet,
                                   forced_in=s.forced_in, forced_out=s.forced_out,
                                   n_facets=s.n_facets, post_filter=post) for s in specs]
     listed = wpm.enumerate_batch(listed_specs, list_mode=True,
-                                 capacities=[max(1, r.count) for r in counted], stream=stream)
+                                 capacities=[capacity] * len(specs), stream=stream)
+    again = [i for i, r in enumerate(listed) if r.status == wpm.ERR_CAPACITY]
+    if again:
+        redo = wpm.enumerate_batch([listed_specs[i] for i in again], list_mode=True,
+                                   capacities=[listed[i].found for i in again], stream=stream)
+        for i, r in zip(again, redo):
+            listed[i] = r
     found = _Found()
     for s, r in zip(specs, listed):
         if r.status != wpm.OK:
@@ -106,7 +109,7 @@ def _search(specs: List[wpm.BatchSpec], post: int, stream=None):
         facets = wpm.candidate_facets(s.kind, s.n, s.m, s.cols)
         flat, off = wpm.complexes_from_masks(facets, r.masks)
         found.add([int(x) for x in s.cols], flat, off)
-    return sum(r.count for r in counted), sum(r.nodes for r in counted), found
+    return sum(r.found for r in listed), sum(r.nodes for r in listed), found
 
 
 def colorable_seeds(n: int, seedness: bool = True, stream=None) -> SeedRun:

@@ -61,7 +61,7 @@ class Output(C.Structure):
                 ("masks", C.POINTER(C.c_uint64)), ("capacity", C.c_uint64),
                 ("masks_on_device", C.c_int32), ("words_per_mask", C.c_int32),
                 ("M", C.c_int32), ("N", C.c_int32), ("status", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("reserved", C.c_int32), ("found", C.c_uint64)]
 
 
 class Instance(C.Structure):
@@ -77,7 +77,9 @@ class Tuning(C.Structure):
                 ("time_limit_ms", C.c_int32), ("feed_levels", C.c_int32),
                 ("hungry_items", C.c_int64), ("donate_levels", C.c_int32),
                 ("donate_every", C.c_int32), ("graph", C.c_int32), ("engine", C.c_int32),
-                ("sweep_max_s", C.c_int32), ("reserved", C.c_int32 * 2)]
+                ("sweep_max_s", C.c_int32), ("ready_polls", C.c_int32),
+                ("idle_polls", C.c_int32), ("test_unpublished", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class RunStats(C.Structure):
@@ -197,11 +199,12 @@ class Result:
     words: int
     masks: Optional[np.ndarray]
     status: int = OK
+    found: int = 0  # WPMs found before the post-filters (= count without them)
 
 
 def _result(o: Output, masks) -> Result:
     return Result(int(o.count), int(o.nodes), int(o.probes), int(o.M), int(o.N),
-                  int(o.words_per_mask), masks, int(o.status))
+                  int(o.words_per_mask), masks, int(o.status), int(o.found))
 
 
 def candidate_facets(kind, n: int, m: int, cols: Sequence[int]) -> np.ndarray:

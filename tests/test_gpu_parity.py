@@ -451,3 +451,35 @@ def test_n11_full_map_against_stored_oracle(W, search):
     g = W.enumerate_batch([W.BatchSpec("dual", 11, 15, inst.cols, cap=-2)], list_mode=False,
                           tuning={"search": search})[0]
     assert (g.count, g.nodes, g.probes) == (c, nd, pr)
+
+
+# ---------------------------------------------------------------------------------------
+# the batched workload's own n = 7 and n = 8 maps on the per-thread kernel the bench times
+# ---------------------------------------------------------------------------------------
+
+def _oracle_lists(args):
+    import oracle as O2
+    kind, n, m, cols = args
+    f = O2.candidate_facets(kind, n, m, cols)
+    return O2.enumerate_dfs(n, m, f, cap=O2.CAP_UBT, capacity=1 << 18)
+
+
+def test_batched_workload_n7_n8_lists_on_per_thread_searches(W):
+    """The first 8 maps of n = 7 and of n = 8 of the 4096-map benchmark batch (seed 0), in
+    one list-mode batch on per-thread searches: the kernel class of n <= 8 with rows of 8
+    (the class the benchmark's tuned run uses). Sorted masks, counts, nodes and probes
+    against the oracle, map by map (the oracle runs in a spawn pool)."""
+    import multiprocessing as mp
+    allm = I.batch_duals(4096, 3, 8, seed=0)
+    maps = [i for i in allm if i.n == 7][:8] + [i for i in allm if i.n == 8][:8]
+    with mp.get_context("spawn").Pool(min(16, len(maps))) as pool:
+        want = pool.map(_oracle_lists, [(i.kind, i.n, i.m, list(i.cols)) for i in maps])
+    specs = [W.BatchSpec(i.kind, i.n, i.m, i.cols, cap=W.CAP_UBT) for i in maps]
+    res = W.enumerate_batch(specs, list_mode=True, capacities=[w[0] for w in want],
+                            tuning={"search": 1})
+    st = W.last_run_stats()
+    assert st["search"] == 1 and st["size_class"] == 4
+    for r, w, i in zip(res, want, maps):
+        assert r.status == 0
+        assert (r.count, r.nodes, r.probes) == tuple(w[:3]), i.label
+        assert np.array_equal(r.masks, w[3])

@@ -21,7 +21,7 @@ _, _, SAMPLES = load_n11_seeds()
 def _oracle_batch(specs, list_mode=True, capacities=None, tuning=None, stream=None,
                   device_out=None, words=None):
     out = []
-    for s in specs:
+    for i, s in enumerate(specs):
         kind = {wpm.PRIMAL: "primal", wpm.DUAL: "dual"}.get(s.kind, s.kind)
         f = O.candidate_facets(kind, s.n, s.m, s.cols)
         cap = O.CAP_UBT if s.cap == wpm.CAP_UBT else s.cap
@@ -29,6 +29,11 @@ def _oracle_batch(specs, list_mode=True, capacities=None, tuning=None, stream=No
                                                   forced_in=s.forced_in, forced_out=s.forced_out,
                                                   list_mode=list_mode, capacity=1 << 16)
         W = max(1, (len(f) + 63) // 64)
+        found = c
+        if list_mode and capacities is not None and c > int(capacities[i]):
+            # as the library does: the count needed, no masks, a per-instance status
+            out.append(wpm.Result(c, nodes, probes, len(f), 0, W, None, wpm.ERR_CAPACITY, c))
+            continue
         if list_mode and s.post_filter and c:
             if s.post_filter & wpm.POST_SEED:
                 keep = O.filter_pic_seed(s.n, s.m, f, masks).astype(bool)
@@ -36,8 +41,26 @@ def _oracle_batch(specs, list_mode=True, capacities=None, tuning=None, stream=No
                 keep = np.array([O.pic_full(s.m, O.masks_to_facets(f, row)) for row in masks])
             masks = masks[keep]
             c = int(keep.sum())
-        out.append(wpm.Result(c, nodes, probes, len(f), 0, W, masks if list_mode else None))
+        out.append(wpm.Result(c, nodes, probes, len(f), 0, W, masks if list_mode else None,
+                              wpm.OK, found))
     return out
+
+
+def test_search_reruns_only_the_maps_that_overflow(on_oracle, monkeypatch):
+    calls = []
+
+    def spy(specs, **kw):
+        calls.append((len(specs), list(kw.get("capacities") or [])))
+        return _oracle_batch(specs, **kw)
+
+    monkeypatch.setattr(wpm, "enumerate_batch", spy)
+    reps = I.idcm_orbit_reps(4)
+    specs = [wpm.BatchSpec("dual", 4, 8, r, cap=wpm.CAP_UBT, base_facet=True) for r in reps]
+    line7, nodes, found = seeds._search(specs, wpm.POST_PIC | wpm.POST_SEED, capacity=600)
+    assert line7 == 20383
+    assert calls[0] == (len(reps), [600] * len(reps))
+    # one more call, for the maps above 600 WPMs only, with room for exactly their count
+    assert len(calls) == 2 and 0 < calls[1][0] < len(reps) and min(calls[1][1]) > 600
 
 
 @pytest.fixture
