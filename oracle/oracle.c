@@ -22,6 +22,11 @@
  *   orc_enumerate_sweep_fixed  the sweep with Section 4.4's initialization: forced-in /
  *                         forced-out facets fix part of X through a column echelon form
  *                         of the kernel basis; only the rest is swept.
+ *   orc_enumerate_sweep_blocks  the sweep over Section 2.1's convenient basis: the same
+ *                         fixed coordinates, then Z blocks over ridges with disjoint parents
+ *                         (at most two generators of a block, within Hamming distance 2 of
+ *                         the fixed part on its pivot rows), the other generators free.
+ *                         orc_convenient_basis reports its shape and |X| (Table 1).
  *   orc_n2_cycle_sets     n = 2 only: a WPM of dimension 1 is a set of vertex-disjoint
  *                         cycles of the candidate graph; counted by graph search.
  *
@@ -50,6 +55,7 @@
  * tuples; output masks have facet j at bit j%64 of word j/64 and are sorted ascending as
  * multiword unsigned integers (the highest word compared first).
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -625,6 +631,325 @@ int orc_enumerate_sweep_fixed(int n, int m, int M, const uint16_t *facets, const
     incidence_free(&I);
     rc = sink_finish(&snk);
     if (st) { st->count = snk.count; st->nodes = swept; st->probes = (uint64_t)n_free; }
+    return rc;
+}
+
+/* ---------------------------------------------------------------------------------- */
+/* O2 with Section 2.1's convenient basis (the Z blocks and the partition I_1..I_l).   */
+/*                                                                                    */
+/* Step 1, the generators: a basis of ker_Z2 A, as for the plain sweep.                 */
+/* Step 2, the fixed coordinates (Section 4.4's initialization): the rows of facets     */
+/*   that must be in K (forced in, and the base facet when it is required) come first,  */
+/*   then the rows of facets that must not be in K, then the rest; the generators are    */
+/*   brought to reduced column echelon form in that row order. A generator led by a     */
+/*   forced-in row has x = 1, one led by a forced-out row x = 0; their sum F is a fixed */
+/*   part of every K, and the other generators are zero on all forced rows.              */
+/* Step 3, the blocks: repeatedly choose a ridge r whose parents P(r) meet the parents  */
+/*   of no ridge chosen before, the one where the unblocked free generators restricted  */
+/*   to the rows P(r) have the largest rank k (the lowest ridge index on ties), while    */
+/*   k >= 2. Column elimination on those rows makes k of them the identity on k pivot    */
+/*   rows of P(r) and the others zero on all of P(r); the pivot rows are then cleared in */
+/*   the earlier blocks' generators by adding the new ones (which are zero on every      */
+/*   earlier P(r), so the earlier blocks keep their form). The k generators form a part */
+/*   I_l of the partition; every other free generator is a part of its own.             */
+/* Step 4, the sets X_l: on a pivot row q of block l, K_q = F_q + x_q, since every other */
+/*   generator is zero there. So K has |S delta c_l| facets among those rows, S the      */
+/*   chosen generators of block l and c_l the pivot rows where F is 1, and a WPM needs   */
+/*   at most 2 (the ridge r^l has degree at most 2): X_l ranges over the S within        */
+/*   Hamming distance 2 of c_l, 1 + k + C(k, 2) choices instead of 2^k (with F = 0 these */
+/*   are the combinations of at most two generators of the block, as in the paper). A    */
+/*   single free generator takes both values.                                           */
+/* Every K = F + B X with X in X_1 x ... x X_l is formed and checked by Proposition 2.1  */
+/* and the properties. nodes reports the combinations visited, |X| = their product.     */
+/* ---------------------------------------------------------------------------------- */
+
+typedef struct {
+    int s, W, M;
+    uint64_t *B;       /* [s * W] generators                                            */
+    int s_i, s_j;      /* generators fixed to 1: [0, s_i); fixed to 0: [s_i, s_j)       */
+    int feasible;      /* the fixed part satisfies every forced row                    */
+    uint64_t *F;       /* [W] the fixed part of K                                       */
+    int n_blocks;
+    int *blk_start;    /* [n_blocks + 1] into blk_col / blk_row                          */
+    int *blk_col;      /* generators of the blocks, block by block                       */
+    int *blk_row;      /* the pivot row (facet) of each block generator                  */
+    int *blk_ridge;    /* [n_blocks] the chosen ridge                                     */
+    int n_single;
+    int *single;       /* free generators outside every block                            */
+} convenient_t;
+
+static void convenient_free(convenient_t *C)
+{
+    free(C->B); free(C->F); free(C->blk_start); free(C->blk_col); free(C->blk_row);
+    free(C->blk_ridge); free(C->single);
+    memset(C, 0, sizeof(*C));
+}
+
+static void xor_col(uint64_t *dst, const uint64_t *src, int W)
+{
+    for (int w = 0; w < W; w++) dst[w] ^= src[w];
+}
+
+static int convenient_build(const incidence_t *I, int n, const uint16_t *facets,
+                            const orc_cond *c, convenient_t *C)
+{
+    memset(C, 0, sizeof(*C));
+    int M = I->M, N = I->N, W = (M + 63) / 64;
+    C->M = M;
+    C->W = W;
+    int rc = gf2_kernel_basis(I, &C->B, &C->s);
+    if (rc) return rc;
+    int s = C->s;
+    uint64_t *B = C->B;
+    int base = c->base_facet ? base_facet_index(n, M, facets) : -1;
+    /* step 2: the row order I, J, rest */
+    char *kind = (char *)calloc(M ? M : 1, 1);   /* 1 forced in, 2 forced out, 3 both */
+    for (int j = 0; j < M; j++) {
+        if ((c->forced_in && bit_of(c->forced_in, j)) || j == base) kind[j] |= 1;
+        if (c->forced_out && bit_of(c->forced_out, j)) kind[j] |= 2;
+    }
+    C->feasible = !(c->base_facet && base < 0);
+    for (int j = 0; j < M; j++)
+        if (kind[j] == 3) C->feasible = 0;
+    int *order = (int *)malloc(sizeof(int) * (M ? M : 1));
+    int n_i = 0, n_j = 0, q = 0;
+    for (int pass = 1; pass <= 3; pass++)
+        for (int j = 0; j < M; j++) {
+            int k = kind[j] == 3 ? 1 : kind[j];
+            if ((pass < 3 && k == pass) || (pass == 3 && k == 0)) {
+                order[q++] = j;
+                n_i += pass == 1;
+                n_j += pass == 2;
+            }
+        }
+    int piv = 0;
+    int *lead = (int *)malloc(sizeof(int) * (s ? s : 1));
+    for (int qq = 0; qq < n_i + n_j && piv < s; qq++) {
+        int j = order[qq];
+        int t = -1;
+        for (int u = piv; u < s; u++)
+            if (bit_of(B + (size_t)u * W, j)) { t = u; break; }
+        if (t < 0) continue;
+        if (t != piv)
+            for (int w = 0; w < W; w++) {
+                uint64_t x = B[(size_t)t * W + w];
+                B[(size_t)t * W + w] = B[(size_t)piv * W + w];
+                B[(size_t)piv * W + w] = x;
+            }
+        for (int u = 0; u < s; u++)
+            if (u != piv && bit_of(B + (size_t)u * W, j)) xor_col(B + (size_t)u * W, B + (size_t)piv * W, W);
+        lead[piv++] = qq;
+    }
+    C->s_i = C->s_j = 0;
+    for (int t = 0; t < piv; t++) {
+        if (lead[t] < n_i) C->s_i++;
+        C->s_j++;
+    }
+    C->F = (uint64_t *)calloc(W, sizeof(uint64_t));
+    for (int t = 0; t < C->s_i; t++) xor_col(C->F, B + (size_t)t * W, W);
+    for (int qq = 0; qq < n_i + n_j; qq++)
+        if (bit_of(C->F, order[qq]) != (qq < n_i)) C->feasible = 0;
+    /* step 3: blocks among the free generators [s_j, s) */
+    int n_free = s - C->s_j;
+    int *unb = (int *)malloc(sizeof(int) * (n_free ? n_free : 1));   /* unblocked free */
+    int n_unb = 0;
+    for (int t = C->s_j; t < s; t++) unb[n_unb++] = t;
+    char *used = (char *)calloc(M ? M : 1, 1);      /* parents of the chosen ridges       */
+    C->blk_start = (int *)calloc((size_t)n_free + 2, sizeof(int));
+    C->blk_col = (int *)malloc(sizeof(int) * (n_free ? n_free : 1));
+    C->blk_row = (int *)malloc(sizeof(int) * (n_free ? n_free : 1));
+    C->blk_ridge = (int *)malloc(sizeof(int) * (n_free ? n_free : 1));
+    int n_bc = 0;
+    for (;;) {
+        int best = -1, best_k = 1;
+        for (int r = 0; r < N; r++) {
+            int np = I->npar[r], clash = 0;
+            const int *P = I->par + (size_t)r * M;
+            for (int a = 0; a < np; a++) clash |= used[P[a]];
+            if (clash || np - 1 <= best_k) continue;   /* the rank is at most np - 1 */
+            /* rank of the unblocked generators restricted to the rows P(r): each one, as an
+               np-bit vector, is reduced by the independent ones kept so far */
+            uint32_t kept[32];
+            int k = 0;
+            for (int u = 0; u < n_unb && k < np; u++) {
+                uint32_t x = 0;
+                for (int a = 0; a < np; a++) x |= (uint32_t)bit_of(B + (size_t)unb[u] * W, P[a]) << a;
+                for (int e = 0; e < k; e++)
+                    if (x & (kept[e] & (~kept[e] + 1u))) x ^= kept[e];
+                if (x) {
+                    for (int e = 0; e < k; e++)   /* keep every lowest bit owned by one vector */
+                        if (kept[e] & (x & (~x + 1u))) kept[e] ^= x;
+                    kept[k++] = x;
+                }
+            }
+            if (k > best_k) { best_k = k; best = r; }
+        }
+        if (best < 0) break;
+        int np = I->npar[best];
+        const int *P = I->par + (size_t)best * M;
+        int b0 = n_bc;
+        for (int a = 0; a < np; a++) {
+            int row = P[a];
+            int pick = -1;
+            for (int u = 0; u < n_unb; u++)
+                if (bit_of(B + (size_t)unb[u] * W, row)) { pick = u; break; }
+            if (pick < 0) continue;
+            int t = unb[pick];
+            unb[pick] = unb[--n_unb];
+            /* clear this row in every other free generator: the unblocked ones, this block's
+               and the earlier blocks' */
+            for (int u = 0; u < n_unb; u++)
+                if (bit_of(B + (size_t)unb[u] * W, row)) xor_col(B + (size_t)unb[u] * W, B + (size_t)t * W, W);
+            for (int e = 0; e < n_bc; e++)
+                if (bit_of(B + (size_t)C->blk_col[e] * W, row))
+                    xor_col(B + (size_t)C->blk_col[e] * W, B + (size_t)t * W, W);
+            C->blk_col[n_bc] = t;
+            C->blk_row[n_bc] = row;
+            n_bc++;
+        }
+        for (int a = 0; a < np; a++) used[P[a]] = 1;
+        C->blk_ridge[C->n_blocks] = best;
+        C->blk_start[C->n_blocks] = b0;
+        C->n_blocks++;
+        C->blk_start[C->n_blocks] = n_bc;
+    }
+    C->n_single = n_unb;
+    C->single = unb;
+    free(kind); free(order); free(lead); free(used);
+    return ORC_OK;
+}
+
+/* Block sizes of the convenient basis and the size of X (Section 2.1; Table 1's |X|
+ * rows). info receives: s, the generators fixed to 1, fixed to 0, feasible, the number of
+ * blocks l, the single generators, then l block sizes. Returns the number of entries, or a
+ * negative error code. *log2_x receives log2 |X| = sum log2(1 + k + C(k, 2)) + singles. */
+int orc_convenient_basis(int n, int m, int M, const uint16_t *facets, const orc_cond *c,
+                         int32_t *info, int info_cap, double *log2_x)
+{
+    (void)m;
+    incidence_t I;
+    int rc = incidence_build(n, M, facets, &I);
+    if (rc) return rc;
+    convenient_t C;
+    rc = convenient_build(&I, n, facets, c, &C);
+    if (rc) { incidence_free(&I); return rc; }
+    int need = 6 + C.n_blocks;
+    if (need > info_cap) { convenient_free(&C); incidence_free(&I); return ORC_ERR_CAPACITY; }
+    info[0] = C.s; info[1] = C.s_i; info[2] = C.s_j - C.s_i; info[3] = C.feasible;
+    info[4] = C.n_blocks; info[5] = C.n_single;
+    double lx = C.n_single;
+    for (int b = 0; b < C.n_blocks; b++) {
+        int k = C.blk_start[b + 1] - C.blk_start[b];
+        info[6 + b] = k;
+        lx += log2(1.0 + k + k * (k - 1) / 2.0);
+    }
+    if (log2_x) *log2_x = lx;
+    convenient_free(&C);
+    incidence_free(&I);
+    return need;
+}
+
+typedef struct {
+    const incidence_t *I;
+    const convenient_t *C;
+    const orc_cond *c;
+    int n, cap;
+    uint64_t *K;        /* [W] the combination being formed */
+    int *deg;
+    char *inK;
+    sink_t *snk;
+    uint64_t visited;
+} blocks_walk_t;
+
+/* The leaf: K = F + the chosen generators, checked from the definition. */
+static void blocks_leaf(blocks_walk_t *b)
+{
+    const incidence_t *I = b->I;
+    int M = I->M, n = b->n;
+    b->visited++;
+    memset(b->deg, 0, sizeof(int) * (I->N ? I->N : 1));
+    int size = 0;
+    for (int j = 0; j < M; j++) {
+        b->inK[j] = (char)bit_of(b->K, j);
+        if (!b->inK[j]) continue;
+        size++;
+        for (int k = 0; k < n; k++) b->deg[I->fr[j * n + k]]++;
+    }
+    for (int r = 0; r < I->N; r++)
+        if (b->deg[r] != 0 && b->deg[r] != 2) return;
+    if (b->cap >= 0 && size > b->cap) return;
+    const orc_cond *c = b->c;
+    for (int j = 0; j < M; j++) {
+        if (c->forced_in && bit_of(c->forced_in, j) && !b->inK[j]) return;
+        if (c->forced_out && bit_of(c->forced_out, j) && b->inK[j]) return;
+    }
+    if (affine_ok(c, M, b->inK)) sink_emit(b->snk, M, b->inK);
+}
+
+static void blocks_singles(blocks_walk_t *b, int i)
+{
+    const convenient_t *C = b->C;
+    if (i == C->n_single) { blocks_leaf(b); return; }
+    const uint64_t *g = C->B + (size_t)C->single[i] * C->W;
+    blocks_singles(b, i + 1);           /* x = 0 */
+    xor_col(b->K, g, C->W);
+    blocks_singles(b, i + 1);           /* x = 1 */
+    xor_col(b->K, g, C->W);
+}
+
+/* Block l: every subset S of its generators within Hamming distance 2 of c_l. */
+static void blocks_block(blocks_walk_t *b, int l)
+{
+    const convenient_t *C = b->C;
+    if (l == C->n_blocks) { blocks_singles(b, 0); return; }
+    int b0 = C->blk_start[l], k = C->blk_start[l + 1] - b0;
+    uint32_t cl = 0;
+    for (int e = 0; e < k; e++) cl |= (uint32_t)bit_of(C->F, C->blk_row[b0 + e]) << e;
+    for (uint32_t S = 0; S < (1u << k); S++) {
+        if (__builtin_popcount(S ^ cl) > 2) continue;
+        for (int e = 0; e < k; e++)
+            if ((S >> e) & 1u) xor_col(b->K, C->B + (size_t)C->blk_col[b0 + e] * C->W, C->W);
+        blocks_block(b, l + 1);
+        for (int e = 0; e < k; e++)
+            if ((S >> e) & 1u) xor_col(b->K, C->B + (size_t)C->blk_col[b0 + e] * C->W, C->W);
+    }
+}
+
+int orc_enumerate_sweep_blocks(int n, int m, int M, const uint16_t *facets, const orc_cond *c,
+                               uint64_t *masks, uint64_t cap_masks, orc_stats *st,
+                               double max_log2_x)
+{
+    int cap = resolve_cap(c->cap, n, m);
+    if (cap == -3) return ORC_ERR_INPUT;
+    incidence_t I;
+    int rc = incidence_build(n, M, facets, &I);
+    if (rc) return rc;
+    convenient_t C;
+    rc = convenient_build(&I, n, facets, c, &C);
+    if (rc) { incidence_free(&I); return rc; }
+    double lx = C.n_single;
+    for (int l = 0; l < C.n_blocks; l++) {
+        int k = C.blk_start[l + 1] - C.blk_start[l];
+        lx += log2(1.0 + k + k * (k - 1) / 2.0);
+    }
+    if (lx > max_log2_x) { convenient_free(&C); incidence_free(&I); return ORC_ERR_INPUT; }
+    int W = C.W;
+    sink_t snk = { masks, cap_masks, 0, W, 0 };
+    blocks_walk_t b;
+    memset(&b, 0, sizeof(b));
+    b.I = &I; b.C = &C; b.c = c; b.n = n; b.cap = cap; b.snk = &snk;
+    b.K = (uint64_t *)calloc(W, sizeof(uint64_t));
+    b.deg = (int *)calloc(I.N ? I.N : 1, sizeof(int));
+    b.inK = (char *)calloc(M ? M : 1, 1);
+    if (C.feasible) {
+        memcpy(b.K, C.F, sizeof(uint64_t) * W);
+        blocks_block(&b, 0);
+    }
+    free(b.K); free(b.deg); free(b.inK);
+    convenient_free(&C);
+    incidence_free(&I);
+    rc = sink_finish(&snk);
+    if (st) { st->count = snk.count; st->nodes = b.visited; st->probes = 0; }
     return rc;
 }
 

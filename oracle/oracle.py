@@ -33,7 +33,7 @@ def build(force: bool = False) -> str:
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-Wall", "-Wextra",
-                           "-o", tmp, _SRC])
+                           "-o", tmp, _SRC, "-lm"])
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -67,6 +67,12 @@ def lib():
             L.orc_enumerate_sweep_fixed.argtypes = [C.c_int, C.c_int, C.c_int, u16p,
                                                     C.POINTER(_Cond), u64p, C.c_uint64,
                                                     C.POINTER(_Stats), C.c_int]
+            L.orc_enumerate_sweep_blocks.argtypes = [C.c_int, C.c_int, C.c_int, u16p,
+                                                     C.POINTER(_Cond), u64p, C.c_uint64,
+                                                     C.POINTER(_Stats), C.c_double]
+            L.orc_convenient_basis.argtypes = [C.c_int, C.c_int, C.c_int, u16p, C.POINTER(_Cond),
+                                               C.POINTER(C.c_int32), C.c_int,
+                                               C.POINTER(C.c_double)]
             L.orc_enumerate_dfs_budget.argtypes = [C.c_int, C.c_int, C.c_int, u16p,
                                                    C.POINTER(_Cond), C.POINTER(_Stats),
                                                    C.c_uint64]
@@ -211,6 +217,33 @@ def enumerate_sweep_fixed(n, m, facets, cap=CAP_NONE, base_facet=False, forced_i
     of free coordinates, masks)."""
     return _enumerate(lib().orc_enumerate_sweep_fixed, n, m, facets, cap, base_facet,
                       forced_in, forced_out, affine, list_mode, capacity, extra=(max_free,))
+
+
+def enumerate_sweep_blocks(n, m, facets, cap=CAP_NONE, base_facet=False, forced_in=None,
+                           forced_out=None, affine=None, list_mode=True, capacity=1 << 12,
+                           max_log2_x=30.0):
+    """O2 with Section 2.1's convenient basis: forced rows fix part of X (Section 4.4), Z
+    blocks over ridges with disjoint parents allow at most two generators each, the other
+    free generators are swept. Returns (count, combinations visited = |X|, 0, masks)."""
+    return _enumerate(lib().orc_enumerate_sweep_blocks, n, m, facets, cap, base_facet,
+                      forced_in, forced_out, affine, list_mode, capacity,
+                      extra=(C.c_double(max_log2_x),))
+
+
+def convenient_basis(n, m, facets, base_facet=False, forced_in=None, forced_out=None):
+    """The convenient basis's shape: dict with s, fixed1, fixed0, feasible, the block sizes,
+    the single free generators, and log2 |X| (Section 2.1; Table 1's |X| rows)."""
+    f = np.ascontiguousarray(facets, dtype=np.uint16)
+    cond, keep = _cond(f.size, CAP_NONE, base_facet, forced_in, forced_out, None)
+    info = np.zeros(512, dtype=np.int32)
+    lx = C.c_double()
+    k = _check(lib().orc_convenient_basis(n, m, f.size, _p(f, C.c_uint16), C.byref(cond),
+                                          _p(info, C.c_int32), info.size, C.byref(lx)),
+               "convenient_basis")
+    del keep
+    return {"s": int(info[0]), "fixed1": int(info[1]), "fixed0": int(info[2]),
+            "feasible": bool(info[3]), "blocks": [int(x) for x in info[6:k]],
+            "singles": int(info[5]), "log2_x": float(lx.value)}
 
 
 def n2_cycle_sets(edges: np.ndarray, max_edges: int = -1) -> int:
