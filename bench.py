@@ -50,9 +50,10 @@ METRIC = "search nodes/sec (batched, 4096 Picard-4 instances n=3..8)"
 UNIT = "nodes/s"
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the depth-first kernel per
-# search node, from one ncu capture of a depth-first launch over 256 maps of this mix
-# (410.7 MB for 2,711,713,518 nodes); the roofline's traffic scales it by the step's nodes.
-TDFS_DRAM_BYTES_PER_NODE = 410.7e6 / 2711713518
+# search node in list mode, from one ncu capture of the current kernel (profiles/); None until
+# the kernel has been captured since its last change. The roofline's traffic scales it by the
+# step's nodes.
+TDFS_DRAM_BYTES_PER_NODE = None
 
 
 # ------------------------------------------------------------------------------------------
@@ -173,6 +174,17 @@ def algorithmic_ops(res, insts):
     child (node or probe) tests its n ridge counters (load, shift, test: 3 ops each), and each
     accepted child updates its n counters on entry and on exit (load, add, store: 6 ops)."""
     return sum(3 * i.n * (r.nodes + r.probes) + 6 * i.n * r.nodes for r, i in zip(res, insts))
+
+
+def survey_ops(res, insts):
+    """The same work counted in 64-bit words as the plan of the path counts it: per node a
+    select over ceil(N/64) words, per tried child its n counter tests, per accepted child n
+    counter updates and ceil(M/64) words of Out."""
+    tot = 0
+    for r, i in zip(res, insts):
+        wn, wm = (r.N + 63) // 64, (r.M + 63) // 64
+        tot += r.nodes * wn + (r.nodes + r.probes) * i.n + r.nodes * (i.n + wm)
+    return tot
 
 
 def run_serving(args):
@@ -382,6 +394,10 @@ def run_ours(args, rank, world, oracle_res=None):
     dev_out = [dev_buf[int(offs[k]):int(offs[k + 1])] for k in range(len(specs))]
     nodes_step = sum(r.nodes for r in res)
     ops_step = algorithmic_ops(res, insts)
+    ops_step_survey = survey_ops(res, insts)
+    # the roofline's peak: integer instructions per second of this GPU, measured (untimed)
+    peak_ops, _ = wpm.int_peak(0)
+    peak_popc, _ = wpm.int_peak(1)
 
     def step_device():
         return wpm.enumerate_batch(specs, list_mode=True, capacities=caps, tuning=tuning,
@@ -451,9 +467,8 @@ def run_ours(args, rank, world, oracle_res=None):
     inst_per_s = world * len(insts) * args.steps / sec
     e2e_t = statistics.median(e2e_times)
     from paper_2301_00806_gb300 import instances as _I  # noqa: F401
-    peak_mhz = 2070.0
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak_ops = n_sm * 128 * peak_mhz * 1e6
+    nominal_ops = n_sm * 128 * 2070.0 * 1e6
     achieved = ops_step * args.steps / (dfs_ms / 1000.0) if dfs_ms > 0 else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -475,13 +490,22 @@ def run_ours(args, rank, world, oracle_res=None):
         "plain_launch": plain,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "int ops/s",
                      "frac": (achieved / peak_ops) if achieved else None,
-                     "traffic": TDFS_DRAM_BYTES_PER_NODE * nodes_step,
+                     "traffic": (TDFS_DRAM_BYTES_PER_NODE * nodes_step
+                                 if TDFS_DRAM_BYTES_PER_NODE else None),
                      "traffic_per": "step (its depth-first launches), scaled from an ncu "
-                                    "capture on 256 maps of the mix by search nodes",
+                                    "capture of the kernel in list mode by search nodes",
                      "kernel": "depth-first pass (tdfs_kernel)",
                      "dfs_launches_per_step": dfs_launches / args.steps,
                      "dfs_ms_per_step": dfs_ms / args.steps,
-                     "peak_from": f"{n_sm} SMs x 128 INT32 lanes x {peak_mhz:.0f} MHz (max clock)"},
+                     "ops_model": "3n per tried child + 6n per accepted child (n ridge counters "
+                                  "tested, then updated on entry and exit); frac uses this",
+                     "ops_per_node": ops_step / nodes_step,
+                     "ops_per_node_word_count": ops_step_survey / nodes_step,
+                     "frac_word_count": (ops_step_survey * args.steps / (dfs_ms / 1000.0) /
+                                         peak_ops) if dfs_ms > 0 else None,
+                     "peak_from": "measured: wpm_int_peak, independent lop3 + add chains on "
+                                  "every SM (popc + xor chains: %.3g ops/s; nominal 152 x 128 "
+                                  "x 2070 MHz: %.3g)" % (peak_popc, nominal_ops)},
         "gpu_launches": launches,
         "clocks": clocks,
         "parity_sample": parity,

@@ -173,16 +173,23 @@ typedef struct {
     int32_t graph;          /* 0: the depth-first pass loop runs as one CUDA graph launch (a
                                conditional while node; not with a time limit or tracing);
                                -1: the host launches each pass                             */
-    int32_t engine;         /* 0: the canonical ridge-driven search; 1: the GF(2) cycle-space
-                               sweep of Section 2.1 (all 2^s elements of ker_Z2 A in Gray-code
-                               order, checked by Proposition 2.1): maps with M <= 256, N <=
-                               1024 and s <= sweep_max_s, else WPM_ERR_LIMIT. Same counts and
-                               lists; `nodes` then counts kernel elements visited, `probes` 0 */
-    int32_t sweep_max_s;    /* largest kernel dimension the sweep accepts (0 = 30, max 48)  */
+    int32_t engine;         /* 0: the canonical ridge-driven search. 1: the GF(2) cycle-space
+                               sweep of Section 2.1 over its convenient basis: rows of forced
+                               facets (and the base facet) fix coordinates of X as in Section
+                               4.4, Z blocks over ridges with disjoint parents allow at most two
+                               generators each, the other generators are swept freely. 2: the
+                               plain sweep of all 2^s elements of ker_Z2 A in Gray-code order.
+                               Both check Proposition 2.1 and the properties; maps with M <=
+                               896, N <= 3200 and s <= 64, else WPM_ERR_LIMIT. Same counts and
+                               lists as the search; `nodes` then counts the combinations
+                               visited (|X| for engine 1, 2^s for engine 2), `probes` 0       */
+    int32_t sweep_max_s;    /* largest log2 of the combinations a sweep may visit (0 = 30,
+                               at most 48); beyond it WPM_ERR_LIMIT                           */
     /* Bounds of the per-thread passes' device waits (they only end waits that end by
        themselves in a correct run). ready_polls: polls of a work item's ready flag before the
        reader gives up; the kernel then returns and the run fails with WPM_ERR_TIMEOUT (0 =
-       2^22, about half a second). idle_polls: fruitless steps after which a search waiting
+       2^22, about half a second; a bound of a few polls can run out before a writer
+       publishes, in a correct run too). idle_polls: fruitless steps after which a search waiting
        for work leaves the pass (0 = 2^14); leaving early never changes counts.           */
     int32_t ready_polls;
     int32_t idle_polls;
@@ -242,9 +249,11 @@ int wpm_enumerate_facets(const uint16_t *facets, int M, int n, int m,
  * Enumerate `count` instances in one batched run on the GPU: all candidate sets are
  * built by one launch, the search runs every instance's frontier together, and outputs
  * are sorted per instance. outs[i] receives instance i (its `status` field holds the
- * per-instance code; the return value is the first failure, or WPM_OK). tuning may be
- * NULL. cuda_stream: a cudaStream_t to run on, or NULL for the library's own stream;
- * the call synchronises that stream before returning.
+ * per-instance code; the return value is the first failure, or WPM_OK; when the run as a
+ * whole fails -- a CUDA error, a ring overflow, a bounded device wait that ran out -- every
+ * instance's status receives that code and no counts are valid). tuning may be NULL.
+ * cuda_stream: a cudaStream_t to run on, or NULL for the library's own stream; the call
+ * synchronises that stream before returning.
  */
 int wpm_enumerate_batch(const wpm_instance *inst, int count, wpm_output *outs, int mode,
                         const wpm_tuning *tuning, void *cuda_stream);
@@ -369,6 +378,18 @@ int wpm_engine_poll(wpm_engine *e, uint64_t *job_ids, int cap);
  * its count. */
 int wpm_engine_result(wpm_engine *e, uint64_t job_id, wpm_output *out);
 void wpm_engine_destroy(wpm_engine *e);
+
+/*
+ * Integer throughput of the current GPU, measured (the paper has no counterpart: this is the
+ * peak of the roofline that the search kernels, bound by integer and logic instructions, are
+ * reported against). op 0: independent chains of lop3 and add instructions (the mix of the
+ * search's bitset and counter updates); op 1: popc and xor. One launch of 4 blocks of 512
+ * threads per SM, each thread running 8 independent chains for `iters` steps, timed with CUDA
+ * events after a warm-up launch. *ops_per_sec receives the instructions per second over all
+ * threads (each lop3, add, popc or xor counted once); *ms (optional) the launch's duration.
+ * The call allocates a small device buffer and a stream of its own.
+ */
+int wpm_int_peak(int op, int iters, double *ops_per_sec, double *ms);
 
 /* ---- misc -------------------------------------------------------------------------- */
 const char *wpm_last_error(void);

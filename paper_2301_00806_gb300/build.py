@@ -48,6 +48,7 @@ def _units(checked: bool):
         (os.path.join(CSRC, "wpm_iso.cpp"), os.path.join(BUILD, f"wpm_iso{tag}.o"), extra),
         (os.path.join(CSRC, "wpm_sphere.cpp"), os.path.join(BUILD, f"wpm_sphere{tag}.o"), extra),
         (os.path.join(CSRC, "wpm_link.cpp"), os.path.join(BUILD, f"wpm_link{tag}.o"), extra),
+        (os.path.join(CSRC, "wpm_peak.cu"), os.path.join(BUILD, f"wpm_peak{tag}.o"), extra),
     ]
     for k in range(N_CLASSES):
         units.append((os.path.join(CSRC, "wpm_class.cu"), os.path.join(BUILD, f"wpm_class{k}{tag}.o"),

@@ -145,7 +145,7 @@ struct PassArgs {
   // grow over the life of the buffer, so stale flags never match.
   uint32_t *ready;                // [ring_cap]
   int rows;                       // per-thread passes, 128 threads: when every instance has
-                                  // at most 8 parents per ridge, 1 for n <= 8, 3 for n <= 9,
+                                  // at most 5 parents per ridge, 1 for n <= 8, 3 for n <= 9,
                                   // 2 for n <= 12 (specialised kernels); else 0
   int donate_every;               // nodes a search searches between two hand-overs
   unsigned long long time_left_ns;  // > 0: searches leave the pass (parking their work) this
@@ -166,22 +166,43 @@ constexpr int kDefaultIdlePolls = 1 << 14;
 constexpr int kParkHeader = 4;  // valid, top entry, depth | base << 16, unused
 
 // GF(2) cycle-space sweep (wpm_sweep.cu): maps with M <= kSweepMaxM candidate facets and
-// N <= kSweepMaxN ridges; kernel bases of dimension up to kSweepMaxS are stored.
-constexpr int kSweepW = 4;          // u64 words of a facet set
+// N <= kSweepMaxN ridges whose kernel has dimension s <= kSweepMaxS.
+constexpr int kSweepW = 14;         // u64 words of a facet set
 constexpr int kSweepMaxM = 64 * kSweepW;
-constexpr int kSweepMaxN = 1024;
-constexpr int kSweepMaxS = 48;
-// Basis of ker A over GF(2) for maps ids[0..n_ids): basis[j] holds kSweepMaxS vectors of
-// kSweepW words, dims[j] the dimension (vectors stored only when it is <= kSweepMaxS).
+constexpr int kSweepMaxN = 3200;    // ridge degrees of 64 threads in shared memory
+constexpr int kSweepMaxS = 64;
+constexpr int kSweepMaxBlocks = 32;  // Z blocks of two or more generators: at most s / 2
+constexpr unsigned long long kSweepChunk = 4096;  // combinations per sweep thread
+
+// Shape of a map's generators after Section 4.4's fixed coordinates and Section 2.1's Z
+// blocks: the sweep visits base + (at most two generators of each block) + (any of the
+// single generators); gens holds the block generators block by block, then the singles.
+struct SweepShape {
+  int32_t s;         // dim ker A
+  int32_t feasible;  // the fixed coordinates satisfy every forced row
+  int32_t n_blocks, n_single, n_gen, pad[3];
+  int8_t block_k[kSweepMaxBlocks];
+  uint64_t base[kSweepW];  // the fixed part plus each block's centre combination
+};
+
+// Basis of ker A over GF(2) for maps ids[0..n_ids): rows_scratch holds n_ids x max_n_ridges
+// x kSweepW words; basis[j] receives kSweepMaxS vectors of kSweepW words, dims[j] the
+// dimension (vectors stored only when it is <= kSweepMaxS).
 cudaError_t launch_kernel_basis(const InstDesc *d_inst, const int32_t *d_ids, int n_ids,
-                                int max_n_ridges, uint64_t *basis, int32_t *dims, cudaStream_t s);
-// All 2^dims[j] combinations of map j, in chunks of 2^clogs[j] Gray-code steps; chunks is the
-// exclusive prefix of the chunk counts (n_ids + 1 entries, the last = total_chunks).
+                                int max_n_ridges, uint64_t *rows_scratch, uint64_t *basis,
+                                int32_t *dims, cudaStream_t s);
+// The generators' final form (mode 1: fixed coordinates and Z blocks; mode 2: the plain
+// basis, every generator single): gens[j] (kSweepMaxS x kSweepW words) and shapes[j].
+cudaError_t launch_convenient(const InstDesc *d_inst, const int32_t *d_ids, int n_ids,
+                              const uint64_t *basis, const int32_t *dims, int mode,
+                              uint64_t *gens, SweepShape *shapes, cudaStream_t s);
+// Every combination of each map (totals[j] of them) in chunks of kSweepChunk; chunks is the
+// exclusive prefix of the maps' chunk counts (n_ids + 1 entries, the last = total_chunks).
 cudaError_t launch_sweep(const InstDesc *d_inst, const int32_t *d_ids, int n_ids,
-                         const uint64_t *basis, const int32_t *dims, const int32_t *clogs,
-                         const unsigned long long *chunks, unsigned long long total_chunks,
-                         int max_n_ridges, const OutDesc *outs, unsigned long long *ctr,
-                         cudaStream_t s);
+                         const uint64_t *gens, const SweepShape *shapes,
+                         const unsigned long long *totals, const unsigned long long *chunks,
+                         unsigned long long total_chunks, int max_n_ridges, const OutDesc *outs,
+                         unsigned long long *ctr, cudaStream_t s);
 
 // Post-filters of Algorithm 4.4 (wpm_post.cu) over the sorted lists of the instances
 // sid[0..ns) (masks [seg[j], seg[j+1]) of the flat order): keep[g] = 1 for each mask g that
@@ -197,9 +218,9 @@ cudaError_t launch_post_compact(const InstDesc *d_inst, const OutDesc *outs, con
                                 unsigned long long *ctr, cudaStream_t s);
 
 // PassArgs::rows for a launch whose largest n is max_n and whose largest parent count of a
-// ridge is at most max_parents (m - n + 1 bounds it).
+// ridge is at most max_parents (m - n + 1 bounds it; 5 for Picard number 4).
 inline int rows_variant(int max_n, int max_parents) {
-  if (max_parents > 8) return 0;
+  if (max_parents > 5) return 0;
   return max_n <= 8 ? 1 : (max_n <= 9 ? 3 : (max_n <= 12 ? 2 : 0));
 }
 

@@ -12,6 +12,7 @@
 //   ->  copy-out.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -215,7 +216,7 @@ struct RunOptions {
   int donate_levels = 0;
   int donate_every = 0;
   int graph = 0;  // < 0: host-driven pass loop
-  int engine = 0;  // 1: GF(2) cycle-space sweep
+  int engine = 0;  // 1: GF(2) cycle-space sweep over the convenient basis; 2: plain sweep
   int sweep_max_s = 0;
   long long hungry_items = 0;
   int ready_polls = 0;
@@ -312,9 +313,9 @@ static cudaError_t launch_pass_graph(Workspace *W, const PassArgs &pa, int k, in
 // basis per map, then every element of the kernel in Gray-code order (wpm_sweep.cu). Counts
 // and list-mode masks land in the same counters and output regions as the search's.
 static int run_sweep(Workspace *W, const InstDesc *hd, const std::vector<int32_t> &valid,
-                     int max_s, cudaStream_t s) {
+                     int engine, int max_log2, cudaStream_t s) {
   const int nv = (int)valid.size();
-  max_s = max_s > 0 ? std::min(max_s, kSweepMaxS) : 30;
+  max_log2 = max_log2 > 0 ? std::min(max_log2, 48) : 30;
   int max_n_ridges = 1;
   for (int i : valid) {
     if (hd[i].M > kSweepMaxM || hd[i].N > kSweepMaxN)
@@ -322,37 +323,60 @@ static int run_sweep(Workspace *W, const InstDesc *hd, const std::vector<int32_t
                   "N <= %d)", i, hd[i].M, hd[i].N, kSweepMaxM, kSweepMaxN);
     max_n_ridges = std::max(max_n_ridges, hd[i].N);
   }
+  const size_t rows_bytes = align_up(8ull * nv * max_n_ridges * kSweepW);
   const size_t basis_bytes = align_up(8ull * nv * kSweepMaxS * kSweepW);
+  const size_t shape_bytes = align_up(sizeof(SweepShape) * nv);
   const size_t dims_bytes = align_up(4ull * nv);
-  const size_t chunk_bytes = align_up(8ull * (nv + 1));
-  WPM_TRY(W->sweep.ensure(basis_bytes + 2 * dims_bytes + chunk_bytes));
-  WPM_TRY(W->h_sweep.ensure(2 * dims_bytes + chunk_bytes));
+  const size_t u64_bytes = align_up(8ull * (nv + 1));
+  // device: rows scratch, basis, generators, shapes, dims, totals, chunk prefix
+  WPM_TRY(W->sweep.ensure(rows_bytes + 2 * basis_bytes + shape_bytes + dims_bytes +
+                          2 * u64_bytes));
+  WPM_TRY(W->h_sweep.ensure(shape_bytes + 2 * u64_bytes));
   char *db = W->sweep.as<char>();
-  uint64_t *basis = (uint64_t *)db;
-  int32_t *dims = (int32_t *)(db + basis_bytes);
-  int32_t *clogs = (int32_t *)(db + basis_bytes + dims_bytes);
-  unsigned long long *chunks = (unsigned long long *)(db + basis_bytes + 2 * dims_bytes);
+  uint64_t *rows = (uint64_t *)db;
+  uint64_t *basis = (uint64_t *)(db + rows_bytes);
+  uint64_t *gens = (uint64_t *)(db + rows_bytes + basis_bytes);
+  SweepShape *shapes = (SweepShape *)(db + rows_bytes + 2 * basis_bytes);
+  int32_t *dims = (int32_t *)(db + rows_bytes + 2 * basis_bytes + shape_bytes);
+  unsigned long long *totals =
+      (unsigned long long *)(db + rows_bytes + 2 * basis_bytes + shape_bytes + dims_bytes);
+  unsigned long long *chunks = totals + (u64_bytes / 8);
   char *hb = W->h_sweep.as<char>();
-  int32_t *hdims = (int32_t *)hb;
-  int32_t *hclogs = (int32_t *)(hb + dims_bytes);
-  unsigned long long *hchunks = (unsigned long long *)(hb + 2 * dims_bytes);
+  SweepShape *hshape = (SweepShape *)hb;
+  unsigned long long *htot = (unsigned long long *)(hb + shape_bytes);
+  unsigned long long *hchunks = htot + (u64_bytes / 8);
   CUDA_TRY(launch_kernel_basis(W->inst.as<InstDesc>(), W->ids.as<int32_t>(), nv, max_n_ridges,
-                               basis, dims, s));
-  t_stats.kernel_launches++;
-  CUDA_TRY(cudaMemcpyAsync(hdims, dims, 4ull * nv, cudaMemcpyDeviceToHost, s));
-  count_copy(hdims, dims, 4ull * nv, cudaMemcpyDeviceToHost);
+                               rows, basis, dims, s));
+  CUDA_TRY(launch_convenient(W->inst.as<InstDesc>(), W->ids.as<int32_t>(), nv, basis, dims,
+                             engine == 2 ? 2 : 1, gens, shapes, s));
+  t_stats.kernel_launches += 2;
+  CUDA_TRY(cudaMemcpyAsync(hshape, shapes, sizeof(SweepShape) * nv, cudaMemcpyDeviceToHost, s));
+  count_copy(hshape, shapes, sizeof(SweepShape) * nv, cudaMemcpyDeviceToHost);
   CUDA_TRY(cudaStreamSynchronize(s));
   hchunks[0] = 0;
   for (int j = 0; j < nv; j++) {
-    if (hdims[j] > max_s)
+    const SweepShape &sh = hshape[j];
+    if (sh.s > kSweepMaxS)
       return fail(WPM_ERR_LIMIT, "sweep: instance %d has a kernel of dimension %d (limit %d)",
-                  valid[j], hdims[j], max_s);
-    hclogs[j] = std::min(hdims[j], 12);  // chunks of 4096 Gray-code steps
-    hchunks[j + 1] = hchunks[j] + (1ull << (hdims[j] - hclogs[j]));
+                  valid[j], sh.s, kSweepMaxS);
+    // combinations: each block's choices times 2^(single generators)
+    double lg = sh.n_single;
+    unsigned long long outer = 1;
+    for (int l = 0; l < sh.n_blocks; l++) {
+      const int k = sh.block_k[l];
+      const unsigned long long c = 1ull + k + (unsigned long long)k * (k - 1) / 2;
+      lg += std::log2((double)c);
+      outer *= c;
+    }
+    if (lg > max_log2 + 1e-9)
+      return fail(WPM_ERR_LIMIT, "sweep: instance %d needs 2^%.1f combinations (limit 2^%d)",
+                  valid[j], lg, max_log2);
+    htot[j] = sh.feasible ? (outer << sh.n_single) : 0;
+    hchunks[j + 1] = hchunks[j] + (htot[j] + kSweepChunk - 1) / kSweepChunk;
   }
-  CUDA_TRY(cudaMemcpyAsync(clogs, hclogs, dims_bytes + chunk_bytes, cudaMemcpyHostToDevice, s));
-  count_copy(clogs, hclogs, dims_bytes + chunk_bytes, cudaMemcpyHostToDevice);
-  CUDA_TRY(launch_sweep(W->inst.as<InstDesc>(), W->ids.as<int32_t>(), nv, basis, dims, clogs,
+  CUDA_TRY(cudaMemcpyAsync(totals, htot, 2 * u64_bytes, cudaMemcpyHostToDevice, s));
+  count_copy(totals, htot, 2 * u64_bytes, cudaMemcpyHostToDevice);
+  CUDA_TRY(launch_sweep(W->inst.as<InstDesc>(), W->ids.as<int32_t>(), nv, gens, shapes, totals,
                         chunks, hchunks[nv], max_n_ridges, W->outd.as<OutDesc>(),
                         W->ctr.as<unsigned long long>(), s));
   t_stats.kernel_launches++;
@@ -571,8 +595,8 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
   CUDA_TRY(cudaMemcpyAsync(W->ids.p, hids, 4ull * n_valid, cudaMemcpyHostToDevice, s));
   count_copy(W->ids.p, hids, 4ull * n_valid, cudaMemcpyHostToDevice);
   bool timed_out = false;
-  if (opt.engine == 1) {
-    WPM_TRY(run_sweep(W, hd, valid, opt.sweep_max_s, s));
+  if (opt.engine == 1 || opt.engine == 2) {
+    WPM_TRY(run_sweep(W, hd, valid, opt.engine, opt.sweep_max_s, s));
     t_stats.search = 0;
   } else {
     QueueCtl *hq = W->h_q.as<QueueCtl>();
@@ -605,13 +629,12 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
     pa.park = search == kSearchThread ? W->park.as<uint32_t>() : nullptr;
     pa.ready = search == kSearchThread ? W->ready.as<uint32_t>() : nullptr;
   if (search == kSearchThread) {
-    int max_n = 0;
-    bool few_parents = true;  // every ridge has at most 8 parents (parents rows of 8)
+    int max_n = 0, max_par = 0;  // m - n + 1 bounds a ridge's parents
     for (int i : valid) {
       max_n = std::max(max_n, hd[i].n);
-      few_parents &= hd[i].pstride == 8;
+      max_par = std::max(max_par, hd[i].m - hd[i].n + 1);
     }
-    pa.rows = rows_variant(max_n, few_parents ? 8 : 16);
+    pa.rows = rows_variant(max_n, max_par);
   }
     pa.hungry = opt.hungry_items > 0 ? (unsigned long long)opt.hungry_items
                                       : (unsigned long long)n_searches;
@@ -1147,7 +1170,10 @@ int wpm_enumerate_batch(const wpm_instance *inst, int count, wpm_output *outs, i
   for (size_t j = 0; j < hi.size(); j++) o2[j] = outs[where[j]];
   std::vector<InstResult> res;
   const int rc = run(W, hi, options_from(tuning, mode), s, o2.data(), res, nullptr);
-  if (rc != WPM_OK) return rc;
+  if (rc != WPM_OK) {  // the run as a whole failed: no instance has a result
+    for (size_t j = 0; j < hi.size(); j++) outs[where[j]].status = rc;
+    return rc;
+  }
   int first = WPM_OK;
   for (size_t j = 0; j < hi.size(); j++) {
     fill_output(res[j], &outs[where[j]]);

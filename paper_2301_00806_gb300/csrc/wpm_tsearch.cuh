@@ -39,15 +39,16 @@
 namespace wpm {
 namespace ts {
 
-// ROWS: 0 for any instance; otherwise every instance of the launch has ridges of at most 8
-// parents and facet rows of at most 8 ridges (1: n <= 8, the second halves of the rows are
-// never read), 9 ridges (3: n <= 9) or 12 ridges (2: n <= 12). The variants need fewer
-// registers and run no predicated loop iterations that no instance uses.
+// ROWS: 0 for any instance; otherwise every instance of the launch has ridges of at most 5
+// parents (m - n <= 4, Picard number 4 or less) and facet rows of at most 8 ridges (1: n <=
+// 8, the second halves of the rows are never read), 9 ridges (3: n <= 9) or 12 ridges (2:
+// n <= 12). The variants need fewer registers and run no predicated loop iterations that
+// no instance uses.
 template <int MW_, int NW_, int TPB_, int ROWS_ = 0>
 struct TCls {
   static constexpr int MW = MW_, NW = NW_, TPB = TPB_;
   static constexpr bool kSmall = ROWS_ == 1;         // rows of 8
-  static constexpr bool kFewParents = ROWS_ != 0;    // parents rows of 8
+  static constexpr bool kFewParents = ROWS_ != 0;    // at most 5 parents (rows of 8)
   static constexpr int kMaxRidges = ROWS_ == 1 ? 8 : (ROWS_ == 3 ? 9 : (ROWS_ == 2 ? 12 : 16));
   static constexpr int SW = (NW + 31) / 32;
   static constexpr bool kSummReg = NW <= 64;
@@ -170,13 +171,17 @@ struct TSearch {
 
   // Add (sign = 1) or remove (sign = -1) facet p, whose row is (a, b).
   __device__ __forceinline__ void apply(int p, const uint4 &a, const uint4 &b, int sign) {
+    {
+      const uint32_t sb = (uint32_t)__cvta_generic_to_shared(sm);
 #pragma unroll
-    for (int k = 0; k < 8; k++) {
-      if (k < n) {
-        const int r = row_at(a, b, k), w = r >> 4;
-        const uint32_t v = cnt(w) + (uint32_t)sign * (1u << ((r & 15) * 2));
-        cnt(w) = v;
-        set_summ(w, v);
+      for (int k = 0; k < 8; k++) {
+        if (k < n) {
+          const int r = row_at(a, b, k), w = r >> 4;
+          const uint32_t d = (uint32_t)sign << ((r & 15) * 2);
+          uint32_t old;
+          asm volatile("atom.shared.add.u32 %0, [%1], %2;" : "=r"(old) : "r"(sb + (uint32_t)w * (K::TPB * 4u)), "r"(d) : "memory");
+          set_summ(w, old + d);
+        }
       }
     }
     if (!K::kSmall && n > 8) {
@@ -190,8 +195,8 @@ struct TSearch {
         }
       }
     }
-    if (sign > 0) inb(p >> 5) |= 1u << (p & 31);
-    else inb(p >> 5) &= ~(1u << (p & 31));
+    if (sign > 0) atomicOr(&inb(p >> 5), 1u << (p & 31));
+    else atomicAnd(&inb(p >> 5), ~(1u << (p & 31)));
     size += sign;
     for (int e = 0; e < n_aff; e++) {
       const long long c = I->aff_coef[e * M + p];
@@ -224,6 +229,19 @@ struct TSearch {
 
   // Set (on) or clear Out bits of the parents in mask `m` of the row (a, b).
   __device__ __forceinline__ void out_bits(uint32_t m, const uint4 &a, const uint4 &b, bool on) {
+    if (K::kFewParents) {
+#pragma unroll
+      for (int s = 0; s < 5; s++) {
+        if ((m >> s) & 1u) {
+          const int q = row_at(a, b, s);
+          const uint32_t bit = 1u << (q & 31);
+          const uint32_t ad = (uint32_t)__cvta_generic_to_shared(&outb(q >> 5));
+          if (on) asm volatile("red.shared.or.b32 [%0], %1;" :: "r"(ad), "r"(bit) : "memory");
+          else asm volatile("red.shared.and.b32 [%0], %1;" :: "r"(ad), "r"(~bit) : "memory");
+        }
+      }
+      return;
+    }
     while (m) {
       const int s = __ffs(m) - 1;
       m &= m - 1;
@@ -272,7 +290,7 @@ struct TSearch {
       ridge_row(r, na, nb);
       uint32_t U = 0;
 #pragma unroll
-      for (int s = 0; s < 8; s++) {
+      for (int s = 0; s < (K::kFewParents ? 5 : 8); s++) {
         const int q = row_at(na, nb, s);
         if (q != 0xFFFF && !decided(q)) U |= 1u << s;
       }
@@ -534,7 +552,7 @@ __global__ void __maxnreg__(96) tdfs_kernel(PassArgs a) {
   // back to level base.
   int depth = 0, base = 0;
   uint32_t top = 0;
-  long long pass_nodes = 0, next_check = 63, next_give = 0;
+  long long pass_nodes = 0, next_check = 511, next_give = 0;
   // stop: leave the pass this iteration; counted: the leaving search adds itself to
   // q->exited (a waiting search is already counted in q->waiting)
   bool active = true, stop = false, counted = false, waiting = false;
@@ -579,7 +597,7 @@ __global__ void __maxnreg__(96) tdfs_kernel(PassArgs a) {
         counted = true;
         continue;
       }
-      if (waiting && busy && (++polls & 3)) continue;  // poll every 4th step beside busy lanes
+      if (waiting && busy && (++polls & 31)) continue;  // poll every 4th step beside busy lanes
       // take tickets for the lanes here (warp-aggregated; never past the tail). Waiting
       // lanes stop being counted as waiting before the take, so a search that sees every
       // search waiting or gone and no item left knows that no more items can come.
@@ -673,7 +691,7 @@ __global__ void __maxnreg__(96) tdfs_kernel(PassArgs a) {
     }
     // ---- every 64 nodes: end of the pass (budget, time, full ring), or hand-over
     if (pass_nodes >= next_check) {
-      next_check = pass_nodes + 64;
+      next_check = pass_nodes + 512;
       const bool end = pass_nodes >= a.budget || vload(&q->full) || global_ns() >= t_end;
       const unsigned long long t = vload(&q->tail), h = vload(&q->head);
       const unsigned long long items = t > h ? t - h : 0;
@@ -764,6 +782,7 @@ __global__ void __maxnreg__(96) tdfs_kernel(PassArgs a) {
     // candidate inside the step was measured slower: each extra table read then stalls the
     // whole warp.)
     int p = -1;
+    bool skip = false;
     if (!(top >> 31)) {
       const uint32_t U = top & 0x7FFFu;
       const int cur = (top >> 15) & 15;
@@ -775,52 +794,69 @@ __global__ void __maxnreg__(96) tdfs_kernel(PassArgs a) {
         p = row_at(S.tp0, S.tp1, k);
       }
     } else {
-      p = S.next_free(top & 0xFFF);
-      if (p >= 0) top = (top & ~0xFFFu) | (uint32_t)(p + 1);
+      // one word of the undecided facets at or above start per step
+      const int start = (int)(top & 0xFFF);
+      if (start < S.M) {
+        const int w = start >> 5;
+        const uint32_t x = ~(S.inb(w) | S.outb(w)) & (kFull << (start & 31));
+        if (x) {
+          p = w * 32 + __ffs(x) - 1;
+          top = (top & ~0xFFFu) | (uint32_t)(p + 1);
+        } else {
+          const int nxt = min((w + 1) * 32, S.M);
+          top = (top & ~0xFFFu) | (uint32_t)nxt;
+          skip = nxt < S.M;
+        }
+      }
     }
     const bool trying = p >= 0;
-    uint4 fa, fb;
-    if (!trying) {
+    const bool popping = !trying && !skip;
+    if (popping) {
       depth--;
       if (depth == base) {
         depth = 0;
         base = 0;
         S.flush();
-        continue;
+      } else {
+        top = stk[(depth - 1) * stride];
+        S.use_entry(top);
+        // the child of `top` that is applied: slot cur of its ridge, or facet start - 1
+        p = (top >> 31) ? (int)(top & 0xFFF) - 1 : row_at(S.tp0, S.tp1, (top >> 15) & 15);
       }
-      top = stk[(depth - 1) * stride];
-      S.use_entry(top);
-      // the child of `top` that is applied: slot cur of its ridge, or facet start - 1
-      p = (top >> 31) ? (int)(top & 0xFFF) - 1 : row_at(S.tp0, S.tp1, (top >> 15) & 15);
     }
-    S.facet_row(p, fa, fb);
-    if (trying && !S.child_ok(p, fa, fb)) {
-      S.probes++;
-      continue;
+    bool acc = false;
+    if (p >= 0) {
+      uint4 fa, fb;
+      S.facet_row(p, fa, fb);
+      const bool ok = !trying || S.child_ok(p, fa, fb);
+      if (!ok) S.probes++;
+      if (ok) {
+        S.apply(p, fa, fb, trying ? 1 : -1);
+        if (!(top >> 31)) {
+          const int k = (top >> 15) & 15;
+          S.out_bits((top & 0x7FFFu) & ~(1u << k), S.tp0, S.tp1, trying);
+        } else {
+          S.floor_ = trying ? p : (int)((top >> 12) & 0xFFF);
+        }
+        acc = trying;
+      }
     }
-    const int sign = trying ? 1 : -1;
-    S.apply(p, fa, fb, sign);
-    if (!(top >> 31)) {
-      const int k = (top >> 15) & 15;
-      S.out_bits((top & 0x7FFFu) & ~(1u << k), S.tp0, S.tp1, trying);
-    } else {
-      S.floor_ = trying ? p : (int)((top >> 12) & 0xFFF);
+    if (acc) {
+      S.nodes++;
+      pass_nodes++;
+      uint4 na, nb;
+      const uint32_t child = S.examine(true, na, nb);
+      if (depth >= a.max_depth) {  // cannot happen when max_depth covers the facet cap
+        atomicOr(&a.q->err, 2ull);
+        S.retreat(top);
+      } else {
+        stk[(depth - 1) * stride] = top;
+        top = child;
+        S.tp0 = na;
+        S.tp1 = nb;
+        depth++;
+      }
     }
-    if (!trying) continue;
-    S.nodes++;
-    pass_nodes++;
-    uint4 na, nb;
-    const uint32_t child = S.examine(true, na, nb);
-    if (depth >= a.max_depth) {  // cannot happen when max_depth covers the facet cap
-      atomicOr(&a.q->err, 2ull);
-      S.retreat(top);
-      continue;
-    }
-    stk[(depth - 1) * stride] = top;
-    top = child;
-    S.tp0 = na;
-    S.tp1 = nb;
-    depth++;
   }
   if (a.trace) {
     const unsigned long long dumps = __reduce_add_sync(kFull, (unsigned)t_dump);

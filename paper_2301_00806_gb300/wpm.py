@@ -137,6 +137,8 @@ def lib():
             L.wpm_engine_step.argtypes = [C.c_void_p, C.POINTER(C.c_int)]
             L.wpm_engine_poll.argtypes = [C.c_void_p, u64p, C.c_int]
             L.wpm_engine_result.argtypes = [C.c_void_p, C.c_uint64, C.POINTER(Output)]
+            L.wpm_int_peak.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_double),
+                                       C.POINTER(C.c_double)]
             L.wpm_engine_destroy.argtypes = [C.c_void_p]
             L.wpm_engine_destroy.restype = None
             _lib = L
@@ -466,6 +468,16 @@ def autotune(specs: List[BatchSpec], sample: int = 0, stream=None):
     if r != OK:
         raise _err(r)
     return {f: getattr(best, f) for f, _ in Tuning._fields_ if f != "reserved"}, ms.value
+
+
+def int_peak(op: int = 0, iters: int = 1 << 15):
+    """wpm_int_peak: measured integer instructions per second of the GPU (op 0: lop3 + add
+    chains, op 1: popc + xor chains). Returns (ops/s, ms of the timed launch)."""
+    ops, ms = C.c_double(), C.c_double()
+    r = lib().wpm_int_peak(op, iters, C.byref(ops), C.byref(ms))
+    if r != OK:
+        raise _err(r)
+    return float(ops.value), float(ms.value)
 
 
 def last_run_stats() -> dict:

@@ -50,11 +50,12 @@ def _maps():
 
 def test_static_matches_allocating_entry_point_twice_in_a_row(lib):
     import torch
-    want = {}
-    for inst in _maps():
+    maps = _maps()
+    want = []
+    for inst in maps:
         r, f = _call(lib.wpm_candidate_facets, inst)
         assert r > 0, lib.wpm_last_error()
-        want[id(inst)] = (r, f)
+        want.append((r, f))
     side = torch.cuda.Stream()
     # one warm call (module loading on first use may take device memory), then measure
     _call(lib.wpm_candidate_facets_static, I.fano_primal(0), (None,))
@@ -62,8 +63,7 @@ def test_static_matches_allocating_entry_point_twice_in_a_row(lib):
     free0 = torch.cuda.mem_get_info()[0]
     alloc0 = torch.cuda.memory_allocated()
     for stream in (None, side.cuda_stream):
-        for inst in _maps():
-            want_r, want_f = want[id(inst)]
+        for inst, (want_r, want_f) in zip(maps, want):
             for _ in range(2):
                 got_r, got = _call(lib.wpm_candidate_facets_static, inst, (stream,))
                 assert got_r == want_r, lib.wpm_last_error()
