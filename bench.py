@@ -20,6 +20,9 @@ path (candidate facets, ridges, search, per-instance sort) over the 4096 instanc
          checked against the paper's counts, seconds per n
   paper_n11  Section 4.4's n = 11 construction end to end (114 links, then the paper's
          4 seeds), checked against the paper's counts, seconds
+  paper_sweep  Section 2.1's GF(2) sweeps on the GPU: all 2^s kernel elements vs the convenient
+         basis (Z blocks, fixed coordinates), combinations visited and seconds, on the Fano
+         maps and Table 2's first row at n = 4, 5
   paper_main_theorem  the main theorem's Picard-4 row assembled from the two runs above
          (plus Section 4.3's cross-polytope at n = 4): total against the paper's 3153
   serving  the request loop over the serving engine (continuous batching): Poisson
@@ -187,26 +190,48 @@ def survey_ops(res, insts):
     return tot
 
 
-def run_serving(args):
+def run_serving(args, rate=None, seconds=None, deadline=None):
     """The serving measurement: seeded Poisson arrivals served in real time by the engine."""
     from paper_2301_00806_gb300 import instances as I, serving
-    jobs = I.poisson_jobs(rate=args.serve_rate, duration=args.serve_seconds, n_lo=5, n_hi=9,
-                          seed=args.seed)
-    st = serving.serve(jobs, list_mode=True, max_n=9, deadline_s=args.serve_deadline)
+    rate = args.serve_rate if rate is None else rate
+    seconds = args.serve_seconds if seconds is None else seconds
+    deadline = args.serve_deadline if deadline is None else deadline
+    jobs = I.poisson_jobs(rate=rate, duration=seconds, n_lo=5, n_hi=9, seed=args.seed)
+    st = serving.serve(jobs, list_mode=True, max_n=9, deadline_s=deadline)
     sm = st.summary()
     done_nodes = st.nodes
     return {
-        "workload": f"Poisson arrivals {args.serve_rate:g}/s for {args.serve_seconds:g} s, "
+        "workload": f"Poisson arrivals {rate:g}/s for {seconds:g} s, "
                     f"n~U{{5..9}}, m=n+4 dual maps, UBT cap, full sorted lists",
         "jobs": sm["jobs"], "completed": sm["completed"], "failed": sm["failed"],
         "unfinished_at_deadline": sm["jobs"] - sm["completed"] - sm["failed"],
-        "deadline_s": args.serve_deadline, "wall_s": sm["wall_s"],
+        "deadline_s": deadline, "wall_s": sm["wall_s"],
         "p50_ms": sm["p50_ms"], "p99_ms": sm["p99_ms"], "mean_ms": sm["mean_ms"],
         "jobs_per_s": sm["jobs_per_s"], "nodes_per_s": sm["nodes_per_s"],
         "mean_nodes_per_completed_job": done_nodes / max(1, sm["completed"]),
         "engine_steps": sm["engine_steps"], "max_active_jobs": sm["max_active_jobs"],
         "latency": "completion minus arrival, over the jobs completed by the deadline",
     }
+
+
+def run_serving_batched(args):
+    """The serving workload's jobs (the sustained run's arrivals), all at once through one
+    batched call: the nodes/s the same job mix reaches without arrivals, the reference the
+    served throughput is compared with."""
+    import torch
+    from paper_2301_00806_gb300 import instances as I, wpm
+    jobs = I.poisson_jobs(rate=args.serve_sustained_rate, duration=args.serve_sustained_seconds,
+                          n_lo=5, n_hi=9, seed=args.seed)
+    specs = [wpm.BatchSpec("dual", j.n, j.m, j.cols, cap=wpm.CAP_UBT) for j in jobs]
+    counts = wpm.enumerate_batch(specs, list_mode=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = wpm.enumerate_batch(specs, list_mode=True, capacities=[max(1, r.count) for r in counts],
+                              words=[r.words for r in counts])
+    dt = time.perf_counter() - t0
+    nodes = sum(r.nodes for r in res)
+    return {"jobs": len(jobs), "nodes": nodes, "seconds": dt, "nodes_per_s": nodes / dt,
+            "mode": "one wpm_enumerate_batch call, full sorted lists to host memory"}
 
 
 # Table 1 of the paper: time per IDCM orbit of its kernel sweep under the upper-bound cap,
@@ -340,6 +365,41 @@ def run_paper_table1(stream):
                         "each n one batched call timed end to end on the host",
             "paper_hardware": "Nvidia Quadro A5000, kernel-combination sweep (Algorithm 2.2); "
                               "n = 11 is the paper's estimate",
+            "rows": rows}
+
+
+def run_paper_sweep(stream):
+    """The GF(2) sweeps of Section 2.1 on the GPU: the plain sweep of all 2^s kernel elements
+    (engine 2) against the sweep over the convenient basis (engine 1: fixed coordinates, Z
+    blocks), on the Fano maps and on Table 2's first row at n = 4 and n = 5 (one map per IDCM
+    orbit, base facet and cap); combinations visited, seconds, and the WPM totals, which must
+    equal the paper's (and the search's)."""
+    import torch
+    from paper_2301_00806_gb300 import instances as I, wpm
+    cases = [("fano_n3", [wpm.BatchSpec(i.kind, i.n, i.m, i.cols, cap=wpm.CAP_UBT)
+                          for i in (I.fano_primal(s) for s in range(16))], 16 * 666),
+             ("table2_n4", [wpm.BatchSpec("dual", 4, 8, r, cap=wpm.CAP_UBT, base_facet=True)
+                            for r in I.idcm_orbit_reps(4)], TABLE2[4][0]),
+             ("table2_n5", [wpm.BatchSpec("dual", 5, 9, r, cap=wpm.CAP_UBT, base_facet=True)
+                            for r in I.idcm_orbit_reps(5)], TABLE2[5][0])]
+    rows = []
+    for name, specs, want in cases:
+        row = {"case": name, "maps": len(specs), "paper_or_expected": want}
+        for label, tun in (("plain", {"engine": 2}), ("blocks", {"engine": 1}),
+                           ("search", {})):
+            wpm.enumerate_batch(specs[:1], list_mode=False, tuning=tun or None, stream=stream)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            res = wpm.enumerate_batch(specs, list_mode=False, tuning=tun or None, stream=stream)
+            dt = time.perf_counter() - t0
+            row[label] = {"wpms": sum(r.count for r in res), "visited": sum(r.nodes for r in res),
+                          "seconds": dt}
+        row["exact"] = row["plain"]["wpms"] == row["blocks"]["wpms"] == row["search"]["wpms"] == want
+        row["blocks_over_plain_visited"] = row["blocks"]["visited"] / row["plain"]["visited"]
+        rows.append(row)
+    return {"workload": "Section 2.1 sweeps: all 2^s elements of ker A (engine 2) vs the "
+                        "convenient basis (engine 1); 'visited' = combinations (sweeps) or "
+                        "search nodes (search)", "all_exact": all(r["exact"] for r in rows),
             "rows": rows}
 
 
@@ -514,12 +574,19 @@ def run_ours(args, rank, world, oracle_res=None):
         line["plain_configs"] = run_plain_configs(stream)
         line["paper_table1"] = run_paper_table1(stream)
         line["paper_table2"] = _guarded(run_paper_table2, stream)
+        line["paper_sweep"] = _guarded(run_paper_sweep, stream)
         line["paper_n11"] = _guarded(run_paper_n11, stream)
         if "rows" in line["paper_table2"] and "n11_seeds" in line["paper_n11"]:
             line["paper_main_theorem"] = _guarded(run_main_theorem, line["paper_table2"],
                                                   line["paper_n11"], stream)
     if world == 1 and args.serve_seconds > 0:
         line["serving"] = run_serving(args)
+    if world == 1 and args.serve_sustained_seconds > 0:
+        # a rate the GPU sustains: latency is then service time, not queueing
+        line["serving_sustained"] = run_serving(args, rate=args.serve_sustained_rate,
+                                                seconds=args.serve_sustained_seconds,
+                                                deadline=2 * args.serve_sustained_seconds + 30)
+        line["serving_batched_reference"] = _guarded(run_serving_batched, args)
     return line
 
 
@@ -543,6 +610,10 @@ def main():
                     help="serving: seconds of arrivals (0 = no serving run)")
     ap.add_argument("--serve-deadline", type=float, default=90.0,
                     help="serving: seconds after which the loop stops")
+    ap.add_argument("--serve-sustained-rate", type=float, default=60.0,
+                    help="serving at a rate the GPU sustains: arrivals per s")
+    ap.add_argument("--serve-sustained-seconds", type=float, default=30.0,
+                    help="seconds of arrivals at the sustained rate (0 = no such run)")
     ap.add_argument("--out-dir", default=os.path.join(ROOT, "bench_out"),
                     help="where the sampled clock log is written")
     args = ap.parse_args()

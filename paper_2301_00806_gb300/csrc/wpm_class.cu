@@ -30,7 +30,7 @@ namespace wpm {
   }                                                                                         \
   static_assert(WCls<mw, nw>::SMW == ((nw + 2 * mw + 1) & ~1) + 4 * kMaxAffine,           \
                 "state_words() in wpm_kernels.cu must match WCls::SMW");                   \
-  static_assert(ts::TCls<mw, nw, 64>::SMW == nw + 2 * mw + (nw <= 64 ? 0 : (nw + 31) / 32), \
+  static_assert(ts::TCls<mw, nw, 64>::SMW == nw + 2 * mw + (nw <= 96 ? 0 : (nw + 31) / 32), \
                 "tstate_words() in wpm_kernels.cu must match TCls::SMW");
 WPM_ONE_CLASS(X, WPM_CLASS_ID)
 #undef X

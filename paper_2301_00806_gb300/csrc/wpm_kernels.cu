@@ -350,7 +350,7 @@ int state_words(int k) {  // must equal Cls<mw, nw>::SMW of wpm_search.cuh
 
 int tstate_words(int k) {  // must equal ts::TCls<mw, nw, *>::SMW of wpm_tsearch.cuh
   const int nw = kClasses[k].nw, mw = kClasses[k].mw;
-  return nw + 2 * mw + (nw <= 64 ? 0 : (nw + 31) / 32);
+  return nw + 2 * mw + (nw <= 96 ? 0 : (nw + 31) / 32);
 }
 
 size_t dfs_smem_bytes(int k, int search, int tpb, int max_depth) {

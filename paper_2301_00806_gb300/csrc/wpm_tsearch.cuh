@@ -28,7 +28,8 @@
 // dynamically indexed access of a warp hits 32 distinct banks:
 //   cnt[NW]  ridge degrees, 2 bits per ridge, 16 ridges per word (values 0, 1, 2)
 //   inb[MW]  In; outb[MW] Out (bits >= M set)
-//   summ[SW] one bit per cnt word that holds a degree-1 ridge (a register when NW <= 64)
+//   summ[SW] one bit per cnt word that holds a degree-1 ridge (three registers, s0..s2,
+//            when NW <= 96)
 // The stack is in global memory, entry L of thread t at [L * n_threads + t].
 #pragma once
 #include <cstdint>
@@ -51,12 +52,19 @@ struct TCls {
   static constexpr bool kFewParents = ROWS_ != 0;    // at most 5 parents (rows of 8)
   static constexpr int kMaxRidges = ROWS_ == 1 ? 8 : (ROWS_ == 3 ? 9 : (ROWS_ == 2 ? 12 : 16));
   static constexpr int SW = (NW + 31) / 32;
-  static constexpr bool kSummReg = NW <= 64;
+  static constexpr bool kSummReg = NW <= 96;  // the summary in up to three registers
   static constexpr int SMW = NW + 2 * MW + (kSummReg ? 0 : SW);
   static constexpr int IW = kItemHeader + 2 * MW + NW;
 };
 
 constexpr unsigned kFull = 0xFFFFFFFFu;
+
+// word with bit `pos` replaced by the low bit of `bit`
+__device__ __forceinline__ uint32_t bfi1(uint32_t word, uint32_t bit, uint32_t pos) {
+  uint32_t r;
+  asm("bfi.b32 %0, %1, %2, %3, 1;" : "=r"(r) : "r"(bit), "r"(word), "r"(pos));
+  return r;
+}
 
 // Stack entries (32 bits).
 //   ridge level: bit 31 = 0 | r << 19 | cur << 15 | U       U: undecided parent slots of r
@@ -82,7 +90,7 @@ __device__ __forceinline__ int row_at(const uint4 &a, const uint4 &b, int k) {
 template <class K>
 struct TSearch {
   uint32_t *sm;
-  uint64_t summ;
+  uint32_t s0, s1, s2;  // the summary when it is in registers: bit w % 32 of s[w / 32]
   // instance
   const InstDesc *I;
   const OutDesc *od;
@@ -108,7 +116,10 @@ struct TSearch {
   __device__ __forceinline__ void set_summ(int w, uint32_t v) {
     const uint32_t has = (v & ~(v >> 1) & 0x55555555u) != 0u;
     if (K::kSummReg) {
-      summ = (summ & ~(1ull << w)) | ((uint64_t)has << w);
+      const uint32_t pos = (uint32_t)w & 31u;
+      if (K::NW <= 32 || w < 32) s0 = bfi1(s0, has, pos);
+      else if (K::NW <= 64 || w < 64) s1 = bfi1(s1, has, pos);
+      else s2 = bfi1(s2, has, pos);
     } else {
       uint32_t &s = summw(w >> 5);
       s = (s & ~(1u << (w & 31))) | (has << (w & 31));
@@ -209,7 +220,9 @@ struct TSearch {
   __device__ __forceinline__ int select_ridge() {
     int w = -1;
     if (K::kSummReg) {
-      if (summ) w = __ffsll((long long)summ) - 1;
+      if (s0) w = __ffs(s0) - 1;
+      else if (K::NW > 32 && s1) w = 32 + __ffs(s1) - 1;
+      else if (K::NW > 64 && s2) w = 64 + __ffs(s2) - 1;
     } else {
       const int sw = (nw + 31) >> 5;
       for (int s = 0; s < sw; s++) {
@@ -393,7 +406,7 @@ struct TSearch {
       const int sw = (nw + 31) >> 5;
       for (int s = 0; s < sw; s++) summw(s) = 0;
     }
-    summ = 0;
+    s0 = s1 = s2 = 0;
     bool ok = true;
     if (fresh) {
       for (int w = 0; w < nw; w++) cnt(w) = 0;
@@ -489,7 +502,7 @@ struct TSearch {
       const int sw = (nw + 31) >> 5;
       for (int s = 0; s < sw; s++) summw(s) = 0;
     }
-    summ = 0;
+    s0 = s1 = s2 = 0;
     for (int w = 0; w < nw; w++) {
       cnt(w) = it[(size_t)(kItemHeader + 2 * K::MW + w) * st];
       set_summ(w, cnt(w));

@@ -55,6 +55,26 @@ def test_jobs_alone_and_in_the_mix_agree(W, max_n, budget):
         assert (g.count, g.nodes, g.probes) == (a.count, a.nodes, a.probes)
         assert np.array_equal(g.masks, a.masks)
     E.close()
+    if max_n == 9 and budget:
+        # and against the oracle: the first n = 7 and n = 8 jobs and the smallest n = 9 job of
+        # the mix (the oracle in a spawn pool)
+        import multiprocessing as mp
+        pick = [next(k for k, j in enumerate(jobs) if j.n == 7),
+                next(k for k, j in enumerate(jobs) if j.n == 8),
+                min((k for k, j in enumerate(jobs) if j.n == 9), key=lambda k: alone[k].nodes)]
+        with mp.get_context("spawn").Pool(len(pick)) as pool:
+            want = pool.map(_oracle_job, [(jobs[k].n, list(jobs[k].cols)) for k in pick])
+        for k, w in zip(pick, want):
+            g = got[ids[k]]
+            assert (g.count, g.nodes, g.probes) == tuple(w[:3]), jobs[k].n
+            assert np.array_equal(g.masks, w[3])
+
+
+def _oracle_job(args):
+    import oracle as O2
+    n, cols = args
+    f = O2.candidate_facets("dual", n, n + 4, cols)
+    return O2.enumerate_dfs(n, n + 4, f, cap=O2.CAP_UBT, capacity=1 << 18)
 
 
 def test_engine_matches_oracle_with_properties(W):
