@@ -53,10 +53,11 @@ METRIC = "search nodes/sec (batched, 4096 Picard-4 instances n=3..8)"
 UNIT = "nodes/s"
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the depth-first kernel per
-# search node in list mode, from one ncu capture of the current kernel (profiles/); None until
-# the kernel has been captured since its last change. The roofline's traffic scales it by the
-# step's nodes.
-TDFS_DRAM_BYTES_PER_NODE = None
+# search node in list mode, from one ncu capture of the current kernel: one pass over 256 maps
+# of this mix, 361,736,704 + 733,481,984 bytes for 2,711,713,518 nodes (masks written and work
+# handed over included). None whenever the kernel has changed since its capture. The
+# roofline's traffic scales it by the step's nodes.
+TDFS_DRAM_BYTES_PER_NODE = (361736704 + 733481984) / 2711713518
 
 
 # ------------------------------------------------------------------------------------------

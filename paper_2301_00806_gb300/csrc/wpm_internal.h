@@ -172,7 +172,7 @@ constexpr int kSweepMaxM = 64 * kSweepW;
 constexpr int kSweepMaxN = 3200;    // ridge degrees of 64 threads in shared memory
 constexpr int kSweepMaxS = 64;
 constexpr int kSweepMaxBlocks = 32;  // Z blocks of two or more generators: at most s / 2
-constexpr unsigned long long kSweepChunk = 4096;  // combinations per sweep thread
+constexpr unsigned long long kSweepChunkMax = 4096;  // combinations per sweep thread, at most
 
 // Shape of a map's generators after Section 4.4's fixed coordinates and Section 2.1's Z
 // blocks: the sweep visits base + (at most two generators of each block) + (any of the
@@ -196,13 +196,15 @@ cudaError_t launch_kernel_basis(const InstDesc *d_inst, const int32_t *d_ids, in
 cudaError_t launch_convenient(const InstDesc *d_inst, const int32_t *d_ids, int n_ids,
                               const uint64_t *basis, const int32_t *dims, int mode,
                               uint64_t *gens, SweepShape *shapes, cudaStream_t s);
-// Every combination of each map (totals[j] of them) in chunks of kSweepChunk; chunks is the
-// exclusive prefix of the maps' chunk counts (n_ids + 1 entries, the last = total_chunks).
+// Every combination of each map (totals[j] of them) in chunks of `chunk` consecutive ones (a
+// thread each); chunks is the exclusive prefix of the maps' chunk counts (n_ids + 1 entries,
+// the last = total_chunks).
 cudaError_t launch_sweep(const InstDesc *d_inst, const int32_t *d_ids, int n_ids,
                          const uint64_t *gens, const SweepShape *shapes,
                          const unsigned long long *totals, const unsigned long long *chunks,
-                         unsigned long long total_chunks, int max_n_ridges, const OutDesc *outs,
-                         unsigned long long *ctr, cudaStream_t s);
+                         unsigned long long total_chunks, unsigned long long chunk,
+                         int max_n_ridges, const OutDesc *outs, unsigned long long *ctr,
+                         cudaStream_t s);
 
 // Post-filters of Algorithm 4.4 (wpm_post.cu) over the sorted lists of the instances
 // sid[0..ns) (masks [seg[j], seg[j+1]) of the flat order): keep[g] = 1 for each mask g that

@@ -353,7 +353,7 @@ static int run_sweep(Workspace *W, const InstDesc *hd, const std::vector<int32_t
   CUDA_TRY(cudaMemcpyAsync(hshape, shapes, sizeof(SweepShape) * nv, cudaMemcpyDeviceToHost, s));
   count_copy(hshape, shapes, sizeof(SweepShape) * nv, cudaMemcpyDeviceToHost);
   CUDA_TRY(cudaStreamSynchronize(s));
-  hchunks[0] = 0;
+  for (int j = 0; j < nv; j++) htot[j] = 0;
   for (int j = 0; j < nv; j++) {
     const SweepShape &sh = hshape[j];
     if (sh.s > kSweepMaxS)
@@ -372,12 +372,18 @@ static int run_sweep(Workspace *W, const InstDesc *hd, const std::vector<int32_t
       return fail(WPM_ERR_LIMIT, "sweep: instance %d needs 2^%.1f combinations (limit 2^%d)",
                   valid[j], lg, max_log2);
     htot[j] = sh.feasible ? (outer << sh.n_single) : 0;
-    hchunks[j + 1] = hchunks[j] + (htot[j] + kSweepChunk - 1) / kSweepChunk;
   }
+  // chunk length: about 64K chunks over the run (a thread each), 64 to 4096 combinations
+  unsigned long long all = 0;
+  for (int j = 0; j < nv; j++) all += htot[j];
+  unsigned long long chunk = 64;
+  while (chunk < kSweepChunkMax && chunk * 65536ull < all) chunk *= 2;
+  hchunks[0] = 0;
+  for (int j = 0; j < nv; j++) hchunks[j + 1] = hchunks[j] + (htot[j] + chunk - 1) / chunk;
   CUDA_TRY(cudaMemcpyAsync(totals, htot, 2 * u64_bytes, cudaMemcpyHostToDevice, s));
   count_copy(totals, htot, 2 * u64_bytes, cudaMemcpyHostToDevice);
   CUDA_TRY(launch_sweep(W->inst.as<InstDesc>(), W->ids.as<int32_t>(), nv, gens, shapes, totals,
-                        chunks, hchunks[nv], max_n_ridges, W->outd.as<OutDesc>(),
+                        chunks, hchunks[nv], chunk, max_n_ridges, W->outd.as<OutDesc>(),
                         W->ctr.as<unsigned long long>(), s));
   t_stats.kernel_launches++;
   return WPM_OK;

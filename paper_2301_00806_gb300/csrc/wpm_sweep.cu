@@ -21,7 +21,8 @@
 //                      (fixed part plus block centres, block sizes, free generators) is kept;
 //   sweep_kernel       every combination: the block digits as an odometer (each choice within
 //                      Hamming distance 2 of the block's centre), the single free generators
-//                      as a Gray code; each thread walks a chunk of consecutive combinations,
+//                      as a Gray code; each thread walks a chunk of consecutive combinations
+//                      (64 to 4096 of them, so that a run has some 64K chunks when it can),
 //                      toggling generators and updating the ridge degrees of the facets they
 //                      flip. Inside ker A every degree is even, so a combination is a WPM
 //                      (Proposition 2.1) when no ridge reaches 4; it is emitted when the
@@ -397,12 +398,13 @@ struct SweepThread {
 };
 
 // chunks: exclusive prefix over the maps of their chunk counts; chunk c of map j covers the
-// combinations [c * L, min((c + 1) * L, total_j)), L = kSweepChunk.
+// combinations [c * L, min((c + 1) * L, total_j)), L = chunk.
 __global__ void __launch_bounds__(kSweepTPB) sweep_kernel(const InstDesc *insts, const int32_t *ids,
                                                         int n_ids, const uint64_t *gens,
                                                         const SweepShape *shapes,
                                                         const unsigned long long *totals,
                                                         const unsigned long long *chunks,
+                                                        unsigned long long chunk,
                                                         const OutDesc *outs,
                                                         unsigned long long *ctr) {
   extern __shared__ uint8_t deg[];  // [N_max * kSweepTPB]
@@ -420,8 +422,8 @@ __global__ void __launch_bounds__(kSweepTPB) sweep_kernel(const InstDesc *insts,
   const uint64_t *G = gens + (size_t)j * kSweepMaxS * kSweepW;
   const int nb = sh.n_blocks, ns = sh.n_single, N = I.N;
   const uint64_t *S = G + (size_t)(sh.n_gen - ns) * kSweepW;  // the single generators
-  const unsigned long long t0 = (g - chunks[j]) * kSweepChunk;
-  const unsigned long long t1 = min(t0 + kSweepChunk, totals[j]);
+  const unsigned long long t0 = (g - chunks[j]) * chunk;
+  const unsigned long long t1 = min(t0 + chunk, totals[j]);
   SweepThread T;
   T.I = &I;
   T.d = deg + threadIdx.x;
@@ -511,8 +513,9 @@ cudaError_t launch_convenient(const InstDesc *d_inst, const int32_t *d_ids, int 
 cudaError_t launch_sweep(const InstDesc *d_inst, const int32_t *d_ids, int n_ids,
                          const uint64_t *gens, const SweepShape *shapes,
                          const unsigned long long *totals, const unsigned long long *chunks,
-                         unsigned long long total_chunks, int max_n_ridges, const OutDesc *outs,
-                         unsigned long long *ctr, cudaStream_t s) {
+                         unsigned long long total_chunks, unsigned long long chunk,
+                         int max_n_ridges, const OutDesc *outs, unsigned long long *ctr,
+                         cudaStream_t s) {
   if (n_ids <= 0 || total_chunks == 0) return cudaSuccess;
   const size_t smem = (size_t)max_n_ridges * kSweepTPB;
   cudaError_t e = cudaFuncSetAttribute(sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -520,7 +523,7 @@ cudaError_t launch_sweep(const InstDesc *d_inst, const int32_t *d_ids, int n_ids
   if (e != cudaSuccess) return e;
   const unsigned long long grid = (total_chunks + kSweepTPB - 1) / kSweepTPB;
   sweep_kernel<<<(unsigned)grid, kSweepTPB, smem, s>>>(d_inst, d_ids, n_ids, gens, shapes, totals,
-                                                       chunks, outs, ctr);
+                                                       chunks, chunk, outs, ctr);
   return cudaGetLastError();
 }
 
