@@ -22,7 +22,7 @@ path (candidate facets, ridges, search, per-instance sort) over the 4096 instanc
          4 seeds), checked against the paper's counts, seconds
   paper_sweep  Section 2.1's GF(2) sweeps on the GPU: all 2^s kernel elements vs the convenient
          basis (Z blocks, fixed coordinates), combinations visited and seconds, on the Fano
-         maps and Table 2's first row at n = 4, 5
+         maps and Table 2's first row at n = 4, 5, 6
   paper_main_theorem  the main theorem's Picard-4 row assembled from the two runs above
          (plus Section 4.3's cross-polytope at n = 4): total against the paper's 3153
   serving  the request loop over the serving engine (continuous batching): Poisson
@@ -372,7 +372,7 @@ def run_paper_table1(stream):
 def run_paper_sweep(stream):
     """The GF(2) sweeps of Section 2.1 on the GPU: the plain sweep of all 2^s kernel elements
     (engine 2) against the sweep over the convenient basis (engine 1: fixed coordinates, Z
-    blocks), on the Fano maps and on Table 2's first row at n = 4 and n = 5 (one map per IDCM
+    blocks), on the Fano maps and on Table 2's first row at n = 4, 5 and 6 (one map per IDCM
     orbit, base facet and cap); combinations visited, seconds, and the WPM totals, which must
     equal the paper's (and the search's)."""
     import torch
@@ -382,7 +382,9 @@ def run_paper_sweep(stream):
              ("table2_n4", [wpm.BatchSpec("dual", 4, 8, r, cap=wpm.CAP_UBT, base_facet=True)
                             for r in I.idcm_orbit_reps(4)], TABLE2[4][0]),
              ("table2_n5", [wpm.BatchSpec("dual", 5, 9, r, cap=wpm.CAP_UBT, base_facet=True)
-                            for r in I.idcm_orbit_reps(5)], TABLE2[5][0])]
+                            for r in I.idcm_orbit_reps(5)], TABLE2[5][0]),
+             ("table2_n6", [wpm.BatchSpec("dual", 6, 10, r, cap=wpm.CAP_UBT, base_facet=True)
+                            for r in I.idcm_orbit_reps(6)], TABLE2[6][0])]
     rows = []
     for name, specs, want in cases:
         row = {"case": name, "maps": len(specs), "paper_or_expected": want}
