@@ -493,14 +493,19 @@ def run_ours(args, rank, world, oracle_res=None):
     assert sum(r.nodes for r in out) == nodes_step
     parity = parity_sample(oracle_res, out, dev_out, words) if oracle_res else None
 
-    # end to end through the C ABI with host buffers (inputs in, sorted lists out)
+    # end to end through the C ABI with host buffers (inputs in, sorted lists out), the
+    # host output arrays allocated once and reused from step to step
     host_caps = caps
+    host_out = [np.empty(max(c, 1) * w, dtype=np.uint64) for c, w in zip(caps, words)]
     e2e_times, h2d, d2h = [], 0, 0
-    for k in range(max(1, args.e2e_steps)):
+    for k in range(max(1, args.e2e_steps) + 1):  # the first call touches the host pages
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         out_h = wpm.enumerate_batch(specs, list_mode=True, capacities=host_caps, tuning=None,
-                                    stream=stream, words=words)  # NULL: the tuned choice
+                                    stream=stream, words=words,
+                                    host_out=host_out)  # NULL: the tuned choice
+        if k == 0:
+            continue
         e2e_times.append(time.perf_counter() - t0)
         st = wpm.last_run_stats()
         h2d, d2h = st["h2d_bytes"], st["d2h_bytes"]

@@ -353,10 +353,13 @@ typedef struct wpm_engine wpm_engine;
 typedef struct {
     int64_t memory_bytes;   /* device memory for job outputs; 0 = 8 GiB                   */
     int32_t max_jobs;       /* concurrent jobs (slots); 0 = 1024                          */
-    int32_t budget;         /* most search nodes per search per step; 0 = 16384           */
+    int32_t budget;         /* most search nodes per search per step; 0 = 2^20            */
     int32_t max_n;          /* largest n admitted (sets the kernel size class and the
                                search depth, the upper-bound cap of n); 0 = 11             */
-    int32_t reserved;
+    int32_t slice_ms;       /* a step's search pass also ends this many milliseconds after it
+                               began (every search parks at that time): it bounds how long a
+                               queued job waits for admission, and passes that end together
+                               leave no tail; 0 = 100 ms, < 0 = the node budget alone      */
 } wpm_engine_config;
 
 /* Create an engine on the current device; stream may be NULL (the engine's own stream). */

@@ -85,6 +85,7 @@ struct wpm_engine {
   int k = 0, search = kSearchThread, tpb = 128, blocks = 0, n_searches = 0, max_depth = 0, iw = 0;
   int max_jobs = 0, max_n = 0;
   long long budget = 4096;
+  int slice_ms = 100;  // > 0: passes also end after this many milliseconds
   size_t slot_bytes = 0;
   unsigned long long ring_cap = 0, dump_limit = 0, idle_limit = 1, hungry = 1;
   unsigned long long parked = 0;  // searches holding parked work after the last pass
@@ -288,6 +289,7 @@ int pass(wpm_engine *e) {
   pa.stack = e->stack.as<uint32_t>();
   pa.aff_scratch = e->aff.as<long long>();
   pa.budget = e->budget;
+  pa.time_left_ns = e->slice_ms > 0 ? (unsigned long long)e->slice_ms * 1000000ull : 0ull;
   pa.idle_limit = e->idle_limit;
   pa.dump_limit = e->dump_limit;
   {  // the row variant the resident jobs allow (m - n + 1 bounds a ridge's parents)
@@ -397,7 +399,8 @@ int wpm_engine_create(const wpm_engine_config *cfg, void *cuda_stream, wpm_engin
   const int64_t mem = cfg && cfg->memory_bytes > 0 ? cfg->memory_bytes : (8ll << 30);
   e->max_jobs = cfg && cfg->max_jobs > 0 ? cfg->max_jobs : 1024;
   e->max_n = cfg && cfg->max_n > 0 ? std::min(cfg->max_n, 12) : 11;
-  e->budget = cfg && cfg->budget > 0 ? cfg->budget : 16384;
+  e->budget = cfg && cfg->budget > 0 ? cfg->budget : (1 << 20);
+  e->slice_ms = !cfg || cfg->slice_ms == 0 ? 100 : (cfg->slice_ms > 0 ? cfg->slice_ms : 0);
   auto bail = [&](int code) {
     wpm_engine_destroy(e);
     return code;

@@ -373,11 +373,12 @@ static int run_sweep(Workspace *W, const InstDesc *hd, const std::vector<int32_t
                   valid[j], lg, max_log2);
     htot[j] = sh.feasible ? (outer << sh.n_single) : 0;
   }
-  // chunk length: about 64K chunks over the run (a thread each), 64 to 4096 combinations
+  // chunk length: up to about 1M chunks over the run (a thread each, so that every SM holds
+  // many 64-thread blocks), 64 to 4096 combinations
   unsigned long long all = 0;
   for (int j = 0; j < nv; j++) all += htot[j];
   unsigned long long chunk = 64;
-  while (chunk < kSweepChunkMax && chunk * 65536ull < all) chunk *= 2;
+  while (chunk < kSweepChunkMax && chunk * (1ull << 20) < all) chunk *= 2;
   hchunks[0] = 0;
   for (int j = 0; j < nv; j++) hchunks[j + 1] = hchunks[j] + (htot[j] + chunk - 1) / chunk;
   CUDA_TRY(cudaMemcpyAsync(totals, htot, 2 * u64_bytes, cudaMemcpyHostToDevice, s));

@@ -22,7 +22,7 @@
 //   sweep_kernel       every combination: the block digits as an odometer (each choice within
 //                      Hamming distance 2 of the block's centre), the single free generators
 //                      as a Gray code; each thread walks a chunk of consecutive combinations
-//                      (64 to 4096 of them, so that a run has some 64K chunks when it can),
+//                      (64 to 4096 of them, so that a run has up to some 1M chunks),
 //                      toggling generators and updating the ridge degrees of the facets they
 //                      flip. Inside ker A every degree is even, so a combination is a WPM
 //                      (Proposition 2.1) when no ridge reaches 4; it is emitted when the
@@ -435,12 +435,13 @@ __global__ void __launch_bounds__(kSweepTPB) sweep_kernel(const InstDesc *insts,
   // the combination t0 from scratch: the base, each block's choice, the singles' Gray code
   uint64_t K0[kSweepW];
   for (int x = 0; x < kSweepW; x++) K0[x] = sh.base[x];
-  int digit[kSweepMaxBlocks];
+  int bk[kSweepMaxBlocks], digit[kSweepMaxBlocks];
+  for (int l = 0; l < nb; l++) bk[l] = sh.block_k[l];
   const unsigned long long inner_mask = ns >= 64 ? ~0ull : (1ull << ns) - 1ull;
   unsigned long long o = ns >= 64 ? 0 : (t0 >> ns);
   int gb = 0;  // first generator of the block
   for (int l = 0; l < nb; l++) {
-    const int k = sh.block_k[l], R = choices(k);
+    const int k = bk[l], R = choices(k);
     digit[l] = (int)(o % (unsigned long long)R);
     o /= (unsigned long long)R;
     const uint32_t set = choice_set(digit[l], k);
@@ -454,6 +455,10 @@ __global__ void __launch_bounds__(kSweepTPB) sweep_kernel(const InstDesc *insts,
     if ((code >> e) & 1ull)
       for (int x = 0; x < kSweepW; x++) K0[x] ^= S[e * kSweepW + x];
   T.toggle(K0);  // from the empty set: every facet of K0 added
+  // the lowest block digit, which moves at every odometer step, stays in registers
+  const int k0 = nb > 0 ? bk[0] : 0, R0 = choices(k0);
+  int d0 = nb > 0 ? digit[0] : 0;
+  uint32_t set0 = choice_set(d0, k0);
   unsigned long long count = 0;
   for (unsigned long long t = t0; t < t1; t++) {
     if (t > t0) {
@@ -464,16 +469,27 @@ __global__ void __launch_bounds__(kSweepTPB) sweep_kernel(const InstDesc *insts,
         // the singles return to none (the Gray code's last word has only the top one), and
         // the block odometer advances
         if (ns > 0) T.toggle(S + (size_t)(ns - 1) * kSweepW);
-        int gl = 0;
-        for (int l = 0; l < nb; l++) {
-          const int k = sh.block_k[l], R = choices(k);
-          const int a = digit[l], a2 = a + 1 == R ? 0 : a + 1;
-          const uint32_t diff = choice_set(a, k) ^ choice_set(a2, k);
-          for (int e = 0; e < k; e++)
-            if ((diff >> e) & 1u) T.toggle(G + (size_t)(gl + e) * kSweepW);
-          digit[l] = a2;
-          gl += k;
-          if (a2 != 0) break;  // no carry
+        if (nb > 0) {
+          const int a2 = d0 + 1;
+          const uint32_t nset = a2 < R0 ? choice_set(a2, k0) : 0u;
+          const uint32_t diff = set0 ^ nset;
+          for (int e = 0; e < k0; e++)
+            if ((diff >> e) & 1u) T.toggle(G + (size_t)e * kSweepW);
+          set0 = nset;
+          d0 = a2 < R0 ? a2 : 0;
+          if (a2 == R0) {  // block 0 wrapped: the carry moves on (rarely far)
+            int gl = k0;
+            for (int l = 1; l < nb; l++) {
+              const int k = bk[l], R = choices(k);
+              const int a = digit[l], b2 = a + 1 == R ? 0 : a + 1;
+              const uint32_t dl = choice_set(a, k) ^ choice_set(b2, k);
+              for (int e = 0; e < k; e++)
+                if ((dl >> e) & 1u) T.toggle(G + (size_t)(gl + e) * kSweepW);
+              digit[l] = b2;
+              gl += k;
+              if (b2 != 0) break;  // no carry
+            }
+          }
         }
       }
     }

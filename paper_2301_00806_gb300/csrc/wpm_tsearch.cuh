@@ -610,7 +610,7 @@ __global__ void __maxnreg__(96) tdfs_kernel(PassArgs a) {
         counted = true;
         continue;
       }
-      if (waiting && busy && (++polls & 31)) continue;  // poll every 4th step beside busy lanes
+      if (waiting && busy && (++polls & 31)) continue;  // poll every 32nd step beside busy lanes
       // take tickets for the lanes here (warp-aggregated; never past the tail). Waiting
       // lanes stop being counted as waiting before the take, so a search that sees every
       // search waiting or gone and no item left knows that no more items can come.

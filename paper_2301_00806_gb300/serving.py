@@ -53,14 +53,14 @@ class ServeStats:
 
 
 def serve(jobs, list_mode: bool = True, max_n: int = 9, max_jobs: int = 1024,
-          budget: int = 16384, memory_bytes: int = 16 << 30, capacity: Dict[int, int] = None,
-          stream=None, deadline_s: float = 0.0, log=None) -> ServeStats:
+          budget: int = 1 << 20, memory_bytes: int = 16 << 30, capacity: Dict[int, int] = None,
+          stream=None, deadline_s: float = 0.0, log=None, slice_ms: int = 0) -> ServeStats:
     """Serve `jobs` (instances with extra['t_arrival'] in seconds) in real time. With
     deadline_s > 0 the loop gives up after that many seconds (unfinished jobs are left out of
     the statistics); `log` (a callable) receives a progress line about every second."""
     capacity = capacity or DEFAULT_CAPACITY
     E = wpm.Engine(memory_bytes=memory_bytes, max_jobs=max_jobs, budget=budget, max_n=max_n,
-                   stream=stream)
+                   stream=stream, slice_ms=slice_ms)
     st = ServeStats(jobs=len(jobs))
     arrival = {}
     meta = {}

@@ -93,7 +93,7 @@ class RunStats(C.Structure):
 
 class EngineConfig(C.Structure):
     _fields_ = [("memory_bytes", C.c_int64), ("max_jobs", C.c_int32), ("budget", C.c_int32),
-                ("max_n", C.c_int32), ("reserved", C.c_int32)]
+                ("max_n", C.c_int32), ("slice_ms", C.c_int32)]
 
 
 _lock = threading.Lock()
@@ -286,14 +286,17 @@ class BatchSpec:
 
 
 def enumerate_batch(specs: List[BatchSpec], list_mode=True, capacities=None, tuning=None,
-                    stream=None, device_out=None, words=None) -> List[Result]:
+                    stream=None, device_out=None, words=None, host_out=None) -> List[Result]:
     """wpm_enumerate_batch over many maps in one batched GPU run.
 
     capacities: per-instance mask capacity (list mode). device_out: optional list of torch
     CUDA uint64 tensors (one per instance, capacity x W) to receive the masks on the device;
     then Result.masks is None and the tensors hold the sorted masks. stream: a torch CUDA
     stream (or raw cudaStream_t int). words: per-instance words per mask (ceil(M/64), e.g.
-    from a counting run) to size host buffers exactly; default 16 (the widest)."""
+    from a counting run) to size host buffers exactly; default 16 (the widest). host_out:
+    optional list of contiguous numpy uint64 arrays (one per instance, at least
+    capacity x words elements) to receive the masks, reusable from call to call; Result.masks
+    is then a view of it."""
     n = len(specs)
     keep = _Keep()
     insts = (Instance * max(n, 1))()
@@ -321,7 +324,15 @@ def enumerate_batch(specs: List[BatchSpec], list_mode=True, capacities=None, tun
                 bufs.append(None)
             else:
                 w = int(words[i]) if words is not None else 16
-                buf = np.empty(max(cap, 1) * w, dtype=np.uint64)
+                if host_out is not None:
+                    buf = host_out[i]
+                    if (buf.dtype != np.uint64 or not buf.flags.c_contiguous
+                            or buf.size < max(cap, 1) * w):
+                        raise ValueError(f"host_out[{i}]: need a contiguous uint64 array of "
+                                         f"{max(cap, 1) * w} elements")
+                    buf = buf.reshape(-1)
+                else:
+                    buf = np.empty(max(cap, 1) * w, dtype=np.uint64)
                 bufs.append(buf)
                 outs[i].masks = _p(buf, C.c_uint64)
                 outs[i].capacity = cap
@@ -359,12 +370,13 @@ class Engine:
     runs one search pass over every resident job; poll() lists finished job ids; result()
     fetches one (a Result; masks in list mode)."""
 
-    def __init__(self, memory_bytes=0, max_jobs=0, budget=0, max_n=0, stream=None):
+    def __init__(self, memory_bytes=0, max_jobs=0, budget=0, max_n=0, stream=None, slice_ms=0):
         cfg = EngineConfig()
         cfg.memory_bytes = memory_bytes
         cfg.max_jobs = max_jobs
         cfg.budget = budget
         cfg.max_n = max_n
+        cfg.slice_ms = slice_ms
         st = None if stream is None else (stream if isinstance(stream, int) else stream.cuda_stream)
         h = C.c_void_p()
         r = lib().wpm_engine_create(C.byref(cfg), C.c_void_p(st) if st else None, C.byref(h))
