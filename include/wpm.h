@@ -153,7 +153,7 @@ typedef struct {
     int64_t ring_items;
     int32_t search;         /* 1: one search per thread, 2: one search per warp, 0: by size
                                (per thread for batches of 16 or more maps of the size
-                               classes of n = 7..9)                                        */
+                               classes of n = 7..10)                                       */
     int32_t profile;        /* nonzero: time every depth-first pass with CUDA events on the
                                run's stream (see wpm_last_run_stats)                       */
     int32_t time_limit_ms;  /* > 0: launch no depth-first pass after this much wall time;

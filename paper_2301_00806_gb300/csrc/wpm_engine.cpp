@@ -21,6 +21,7 @@
 #include <cstring>
 #include <deque>
 #include <map>
+#include <memory>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -70,7 +71,69 @@ struct Job {
   uint64_t count = 0, nodes = 0, probes = 0;
   int M = 0, N = 0, ow = 1;
   size_t pool_off = 0, pool_bytes = 0;
-  std::vector<uint64_t> masks;
+  uint64_t *masks = nullptr;  // count * ow words (list mode): a block of the engine's host cache
+  size_t masks_block = 0;     // that block's size class in bytes (0: no block)
+};
+
+// Finished jobs' sorted lists wait in page-locked host blocks until wpm_engine_result copies
+// them out: copies into page-locked memory run at the link's full rate, several times faster
+// than into pageable memory, and the blocks are reused from job to job (power-of-two size
+// classes from 64 KiB; at most kHostCacheBytes kept free) so that page locking, which costs
+// milliseconds per call, is paid only while the cache warms up. A block that cannot be locked
+// falls back to ordinary memory.
+constexpr size_t kHostCacheBytes = 4ull << 30;
+
+struct HostCache {
+  std::map<size_t, std::vector<void *>> free;  // size class -> free blocks
+  std::map<void *, bool> locked;               // every block handed out or free: page-locked?
+  size_t free_bytes = 0;
+  static size_t size_class(size_t bytes) {
+    size_t c = 64 * 1024;
+    while (c < bytes) c *= 2;
+    return c;
+  }
+  void *take(size_t bytes, size_t &cls) {
+    cls = size_class(bytes);
+    auto it = free.find(cls);
+    if (it != free.end() && !it->second.empty()) {
+      void *p = it->second.back();
+      it->second.pop_back();
+      free_bytes -= cls;
+      return p;
+    }
+    void *p = nullptr;
+    if (cudaHostAlloc(&p, cls, cudaHostAllocDefault) == cudaSuccess) {
+      locked[p] = true;
+      return p;
+    }
+    cudaGetLastError();
+    p = malloc(cls);
+    if (p) locked[p] = false;
+    return p;
+  }
+  void drop(void *p) {
+    auto it = locked.find(p);
+    if (it == locked.end()) return;
+    if (it->second) cudaFreeHost(p);
+    else ::free(p);
+    locked.erase(it);
+  }
+  void give(void *p, size_t cls) {
+    if (!p) return;
+    if (free_bytes + cls > kHostCacheBytes) {
+      drop(p);
+      return;
+    }
+    free[cls].push_back(p);
+    free_bytes += cls;
+  }
+  void release_all() {
+    std::vector<void *> all;
+    for (auto &kv : locked) all.push_back(kv.first);
+    for (void *p : all) drop(p);
+    free.clear();
+    free_bytes = 0;
+  }
 };
 
 }  // namespace
@@ -93,6 +156,7 @@ struct wpm_engine {
   DevBuf inst, outd, ctr, tables, cond, ring, ready, stack, aff, q, ids, seg, pool, park;
   uint32_t epoch = 0;
   PinBuf h_inst, h_outd, h_ctr, h_q, h_ids, h_seg, h_cond;
+  HostCache host_lists;
   size_t pool_bytes = 0;
   std::map<size_t, size_t> free_blocks;  // output pool: offset -> bytes
   std::deque<Job *> pending;
@@ -375,9 +439,11 @@ int retire(wpm_engine *e) {
       CUDA_TRY(launch_sort_pass(e->inst.as<InstDesc>(), e->outd.as<OutDesc>(), e->ids.as<int32_t>(),
                                 ns, e->seg.as<unsigned long long>(), seg.back(), 1ull << 62, 1, e->s));
     for (Job *j : to_sort) {
-      j->masks.resize(j->count * j->ow);
-      CUDA_TRY(cudaMemcpyAsync(j->masks.data(), e->pool.as<char>() + j->pool_off,
-                               8 * j->masks.size(), cudaMemcpyDeviceToHost, e->s));
+      const size_t bytes = 8 * j->count * j->ow;
+      j->masks = (uint64_t *)e->host_lists.take(bytes, j->masks_block);
+      if (!j->masks) return fail(WPM_ERR_NOMEM, "no host memory for a job's list (%zu bytes)", bytes);
+      CUDA_TRY(cudaMemcpyAsync(j->masks, e->pool.as<char>() + j->pool_off, bytes,
+                               cudaMemcpyDeviceToHost, e->s));
     }
     CUDA_TRY(cudaStreamSynchronize(e->s));
   }
@@ -566,8 +632,9 @@ int wpm_engine_result(wpm_engine *e, uint64_t job_id, wpm_output *out) {
                 (unsigned long long)j->count);
       return rc;  // the result stays available for another call
     }
-    if (j->count) memcpy(out->masks, j->masks.data(), 8 * j->masks.size());
+    if (j->count) memcpy(out->masks, j->masks, 8 * j->count * j->ow);
   }
+  e->host_lists.give(j->masks, j->masks_block);
   e->jobs.erase(it);
   delete j;
   return rc;
@@ -577,6 +644,7 @@ void wpm_engine_destroy(wpm_engine *e) {
   if (!e) return;
   if (e->s) cudaStreamSynchronize(e->s);
   for (auto &kv : e->jobs) delete kv.second;
+  e->host_lists.release_all();
   for (DevBuf *b : {&e->inst, &e->outd, &e->ctr, &e->tables, &e->cond, &e->ring, &e->ready,
                     &e->stack, &e->aff, &e->q, &e->ids, &e->seg, &e->pool, &e->park})
     b->release();

@@ -517,14 +517,15 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
   // ---- size class and launch shape ------------------------------------------------
   const int k = pick_size_class(mw_max, nw_max);
   if (k < 0) return fail(WPM_ERR_LIMIT, "no kernel size class holds mw=%d nw=%d", mw_max, nw_max);
-  // per-thread searches for batches of at least 16 maps of the middle size classes (n = 7..9);
+  // per-thread searches for batches of at least 16 maps of the size classes of n = 7..10;
   // per-warp searches for small maps, whose subtrees are too small to keep a thread each
-  // busy, for large ones, where a thread's state would leave too few searches per SM, and for
-  // a few maps alone, which cannot keep some 80,000 per-thread searches fed (measured: 7 maps
-  // of n = 9 run 1.5 times faster per warp, 64 maps 2 times faster per thread)
+  // busy, for n = 11, where a thread's state would leave too few searches per SM, and for a
+  // few maps alone, which cannot keep some 80,000 per-thread searches fed (measured: the 7
+  // IDCM orbits of n = 9 run 1.14 times faster per warp, the 3 of n = 10 1.4 times, the whole
+  // n = 11 map 2.7 times; 16 maps of n = 10 run 1.3 times faster per thread)
   const int search = opt.search == kSearchThread || opt.search == kSearchWarp
                          ? opt.search
-                         : (k >= 3 && k <= 5 && n_valid >= 16 ? kSearchThread : kSearchWarp);
+                         : (k >= 3 && k <= 6 && n_valid >= 16 ? kSearchThread : kSearchWarp);
   int tpb = opt.tpb > 0 ? opt.tpb : (search == kSearchThread ? 128 : 256);
   if (tpb != 64 && tpb != 128 && tpb != 256) tpb = 128;
   int occ = dfs_max_blocks_per_sm(k, search, tpb, max_depth);

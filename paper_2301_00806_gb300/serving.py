@@ -53,7 +53,7 @@ class ServeStats:
 
 
 def serve(jobs, list_mode: bool = True, max_n: int = 9, max_jobs: int = 1024,
-          budget: int = 1 << 20, memory_bytes: int = 16 << 30, capacity: Dict[int, int] = None,
+          budget: int = 1 << 20, memory_bytes: int = 64 << 30, capacity: Dict[int, int] = None,
           stream=None, deadline_s: float = 0.0, log=None, slice_ms: int = 0) -> ServeStats:
     """Serve `jobs` (instances with extra['t_arrival'] in seconds) in real time. With
     deadline_s > 0 the loop gives up after that many seconds (unfinished jobs are left out of
@@ -88,7 +88,7 @@ def serve(jobs, list_mode: bool = True, max_n: int = 9, max_jobs: int = 1024,
             st.steps += 1
             st.max_active = max(st.max_active, active)
             for jid in E.poll():
-                r = E.result(jid, capacity=capacity.get(meta[jid].n, 1 << 16))
+                r = E.result(jid)
                 if r.status == wpm.ERR_CAPACITY:  # resubmit with the exact size, same arrival
                     j = meta[jid]
                     nj = E.submit(j.kind, j.n, j.m, j.cols, cap=wpm.CAP_UBT, list_mode=True,

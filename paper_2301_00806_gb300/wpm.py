@@ -420,27 +420,29 @@ class Engine:
             raise _err(k)
         return [int(x) for x in ids[:k]]
 
-    def result(self, job_id: int, capacity: int = 1 << 16) -> Result:
+    def result(self, job_id: int, capacity: int = 0) -> Result:
+        """The finished job's Result. A list-mode job's masks are fetched in two calls: the
+        first (no buffer) reports the count, the second fills an array of exactly that size
+        (`capacity` is accepted for compatibility and not needed)."""
         list_mode = self._modes.get(job_id, False)
-        while True:
+        o = Output()
+        r = lib().wpm_engine_result(self._h, job_id, C.byref(o))
+        masks = None
+        if r == ERR_CAPACITY and list_mode and o.status == OK:
+            count, w = int(o.count), int(o.words_per_mask)
+            masks = np.empty((count, w), dtype=np.uint64)
             o = Output()
-            buf = None
-            if list_mode:
-                buf = np.zeros(max(capacity, 1) * 16, dtype=np.uint64)
-                o.masks = _p(buf, C.c_uint64)
-                o.capacity = capacity
+            o.masks = _p(masks, C.c_uint64)
+            o.capacity = count
             r = lib().wpm_engine_result(self._h, job_id, C.byref(o))
-            if r == ERR_CAPACITY and list_mode and o.status == OK and o.count > capacity:
-                capacity = int(o.count)
-                continue
-            self._modes.pop(job_id, None)
+        elif list_mode and r == OK and o.status == OK:
+            masks = np.zeros((0, int(o.words_per_mask)), dtype=np.uint64)
+        self._modes.pop(job_id, None)
+        if r != OK and r != o.status:
             masks = None
-            if list_mode and o.status == OK:
-                w = int(o.words_per_mask)
-                masks = buf[: int(o.count) * w].reshape(int(o.count), w).copy()
-            res = _result(o, masks)
-            res.status = int(o.status) if r == OK or r == o.status else r
-            return res
+        res = _result(o, masks)
+        res.status = int(o.status) if r == OK or r == o.status else r
+        return res
 
     def close(self):
         if getattr(self, "_h", None):

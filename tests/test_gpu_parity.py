@@ -483,3 +483,21 @@ def test_batched_workload_n7_n8_lists_on_per_thread_searches(W):
         assert r.status == 0
         assert (r.count, r.nodes, r.probes) == tuple(w[:3]), i.label
         assert np.array_equal(r.masks, w[3])
+
+
+def test_n10_batch_default_is_per_thread_and_exact(W):
+    """16 maps of n = 10 (616 candidate facets each) with no tuning: a batch this size of the
+    n = 10 class runs one search per thread by default. Count, nodes and probes of every map
+    against the oracle's stored results (tests/golden/n10_batch.txt, written by
+    make_n10_batch.py), and the per-warp search gives the same."""
+    rows = load_table("n10_batch.txt")
+    assert [r[0] for r in rows] == list(range(16))
+    specs = [W.BatchSpec("dual", 10, 14, I.single_dual(10, s).cols, cap=W.CAP_UBT)
+             for s, _, _, _ in rows]
+    for tuning, search in ((None, 1), ({"search": 2}, 2)):
+        res = W.enumerate_batch(specs, list_mode=False, tuning=tuning)
+        st = W.last_run_stats()
+        assert st["search"] == search and st["size_class"] == 6
+        for r, (s, c, nd, pr) in zip(res, rows):
+            assert r.status == 0
+            assert (r.count, r.nodes, r.probes) == (c, nd, pr), s
