@@ -9,7 +9,8 @@ path (candidate facets, ridges, search, per-instance sort) over the 4096 instanc
          events on the run's stream (inputs are host-side maps of 64 bytes each; the
          library copies their descriptors in the same step)
   e2e    the same metric through the C ABI with host buffers: the step includes copying
-         the inputs in and every sorted mask list out to pinned host memory
+         the inputs in and every sorted mask list out to the caller's host arrays (through
+         the library's page-locked staging buffer)
 
   plain_configs  the single-map workloads (Fano n = 3 and n = 5 maps, 16 seeds each, full
          lists; the whole n = 11 map, count only), one plain call per map
@@ -497,7 +498,7 @@ def run_ours(args, rank, world, oracle_res=None):
     # host output arrays allocated once and reused from step to step
     host_caps = caps
     host_out = [np.empty(max(c, 1) * w, dtype=np.uint64) for c, w in zip(caps, words)]
-    e2e_times, h2d, d2h = [], 0, 0
+    e2e_times, e2e_parts, h2d, d2h = [], [], 0, 0
     for k in range(max(1, args.e2e_steps) + 1):  # the first call touches the host pages
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -505,10 +506,12 @@ def run_ours(args, rank, world, oracle_res=None):
                                     stream=stream, words=words,
                                     host_out=host_out)  # NULL: the tuned choice
         if k == 0:
+            e2e_first = time.perf_counter() - t0
             continue
         e2e_times.append(time.perf_counter() - t0)
         st = wpm.last_run_stats()
         h2d, d2h = st["h2d_bytes"], st["d2h_bytes"]
+        e2e_parts.append((st["run_ms"], st["copy_out_ms"], st["host_copy_ms"]))
     assert sum(r.nodes for r in out_h) == nodes_step
 
     # the plain path: one instance per call, on a sample of the same batch
@@ -554,7 +557,12 @@ def run_ours(args, rank, world, oracle_res=None):
         "instances_per_s": inst_per_s,
         "nodes_per_step": nodes_step * world,
         "e2e": {"value": world * nodes_step / e2e_t, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_t * 1000.0},
+                "d2h_bytes_per_step": d2h, "ms_per_step": e2e_t * 1000.0,
+                "ms_per_call": [round(t * 1000.0, 1) for t in e2e_times],
+                "first_call_ms": round(e2e_first * 1000.0, 1),
+                "library_ms_per_call": [round(p[0], 1) for p in e2e_parts],
+                "copy_out_ms_per_call": [round(p[1], 1) for p in e2e_parts],
+                "host_copy_ms_per_call": [round(p[2], 1) for p in e2e_parts]},
         "plain_launch": plain,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_ops, "unit": "int ops/s",
                      "frac": (achieved / peak_ops) if achieved else None,

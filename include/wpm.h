@@ -196,7 +196,10 @@ typedef struct {
     int32_t test_unpublished; /* test hook, 0 in normal use: nonzero makes readers of items
                                written during a pass wait for a ready stamp that no writer
                                raises, so every such wait runs out (WPM_ERR_TIMEOUT)        */
-    int32_t reserved;
+    int32_t stage_chunk_words; /* host outputs leave the device in chunks of this many u64
+                               words through two page-locked halves of a staging buffer, one
+                               chunk's device-to-host copy overlapping the copy of the last one
+                               into the caller's buffers (0 = 2^25, 256 MB)                  */
 } wpm_tuning;
 
 /* Statistics of the calling thread's last enumeration run. */
@@ -216,6 +219,11 @@ typedef struct {
     uint64_t d2h_bytes;        /* bytes copied device -> host by the run                       */
     uint64_t graph_launches;   /* CUDA graph launches (the depth-first pass loop run on the
                                   device by a conditional while node)                          */
+    double run_ms;             /* host time of the run, from the checked inputs to the results */
+    double copy_out_ms;        /* host time of the copy-out: gather on the device, the copy to
+                                  the page-locked staging buffer, the copies to host outputs   */
+    double host_copy_ms;       /* the part of copy_out_ms spent copying from the staging buffer
+                                  to the caller's host buffers                                 */
 } wpm_run_stats;
 
 int wpm_last_run_stats(wpm_run_stats *out);

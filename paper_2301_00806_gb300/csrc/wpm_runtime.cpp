@@ -48,6 +48,10 @@ int set_last_error(int code, const char *msg) { return fail(code, "%s", msg); }
 
 void clear_last_error() { t_err.clear(); }
 
+// Host outputs leave the device in chunks of at most this many words (256 MB) through two
+// page-locked halves of the workspace's staging buffer.
+constexpr size_t kStageChunk = 32u << 20;
+
 // Device buffers reused across calls on one device.
 // The depth-first pass loop as an instantiated CUDA graph: a conditional while node whose
 // body is prep, the pass and check. Kept while the pass's arguments stay the same.
@@ -72,6 +76,7 @@ struct Workspace {
   int sms = 0;
   cudaStream_t own = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEvent_t ev_stage[2] = {nullptr, nullptr};  // the two halves of h_stage filled
   PassGraph pg;
   DevBuf inst, outd, ctr, arena, cond, ids, q, ring, ready, stack, aff, park, out, seg, segs, stage,
       sweep, keep;
@@ -86,6 +91,10 @@ struct Workspace {
     for (PinBuf *b : {&h_inst, &h_outd, &h_q, &h_ctr, &h_cond, &h_ids, &h_seg, &h_segs, &h_stage,
                       &h_sweep})
       b->release();
+    for (cudaEvent_t &e : ev_stage) {
+      if (e) cudaEventDestroy(e);
+      e = nullptr;
+    }
   }
 };
 
@@ -222,6 +231,7 @@ struct RunOptions {
   int ready_polls = 0;
   int idle_polls = 0;
   int test_unpublished = 0;
+  long long stage_chunk = 0;
   bool profile = false;
   bool setup_only = false;  // stop after the setup kernel (candidate facets)
 };
@@ -397,6 +407,13 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
   const int n_inst = (int)hi.size();
   res.assign(n_inst, InstResult());
   memset(&t_stats, 0, sizeof(t_stats));
+  struct RunClock {  // run_ms on every way out
+    std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+    ~RunClock() {
+      t_stats.run_ms =
+          std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+  } run_clock;
   if (n_inst == 0) return WPM_OK;
 
   // ---- device layout of the tables and of the caller's conditions --------------------
@@ -901,6 +918,7 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
   }
 
   // ---- copy-out -------------------------------------------------------------------------
+  const auto tc0 = std::chrono::steady_clock::now();
   std::vector<CopySeg> cs;
   std::vector<unsigned long long> cp(1, 0);
   std::vector<int> host_ids;
@@ -912,7 +930,10 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
   size_t stage_words = 0;
   for (int i : host_ids) stage_words += res[i].count * (unsigned long long)hd[i].ow;
   WPM_TRY(W->stage.ensure(8 * stage_words + 256));
-  WPM_TRY(W->h_stage.ensure(8 * stage_words + 256));
+  // the host side of the staging area: two chunks of at most kStageChunk words
+  const size_t chunk = std::min<size_t>(opt.stage_chunk > 0 ? (size_t)opt.stage_chunk : kStageChunk,
+                                        std::max<size_t>(stage_words, 1));
+  WPM_TRY(W->h_stage.ensure(2 * 8 * chunk + 256));
   size_t sw = 0;
   for (int j = 0; j < ns; j++) {
     const int i = sorted_ids[j];
@@ -939,35 +960,63 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
                                (const unsigned long long *)(W->segs.as<char>() +
                                                             sizeof(CopySeg) * cs.size()),
                                cp.back(), s));
-  if (sw) CUDA_TRY(cudaMemcpyAsync(W->h_stage.p, W->stage.p, 8 * sw, cudaMemcpyDeviceToHost, s));
   count_copy(W->h_stage.p, W->stage.p, 8 * sw, cudaMemcpyDeviceToHost);
-  CUDA_TRY(cudaStreamSynchronize(s));
-  // staging -> the caller's host buffers, split over host threads when there is much to move
+
+  // staging -> the caller's host buffers, chunk by chunk through the two halves of h_stage:
+  // the device-to-host copy of chunk c + 1 runs while host threads copy chunk c out (one
+  // copy of the whole list into one large page-locked buffer ran several times slower than
+  // copies of a few hundred MB into a buffer that is reused)
   std::vector<std::pair<size_t, int>> parts;  // (staging word offset, instance)
   size_t total_words = 0;
   for (int i : host_ids) {
     parts.emplace_back(total_words, i);
     total_words += res[i].count * (size_t)hd[i].ow;
   }
-  auto copy_range = [&](size_t lo, size_t hi) {  // staging words [lo, hi)
+  // staging words [lo, hi), held in `src` from word `base` on
+  auto copy_range = [&](size_t lo, size_t hi, const uint64_t *src, size_t base) {
     for (const auto &pi : parts) {
       const size_t a = pi.first, words = res[pi.second].count * (size_t)hd[pi.second].ow;
       const size_t x = std::max(a, lo), y = std::min(a + words, hi);
-      if (x < y)
-        memcpy(outs[pi.second].masks + (x - a), W->h_stage.as<uint64_t>() + x, 8 * (y - x));
+      if (x < y) memcpy(outs[pi.second].masks + (x - a), src + (x - base), 8 * (y - x));
     }
   };
+  for (cudaEvent_t &e : W->ev_stage)
+    if (!e) CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  const size_t n_chunks = (sw + chunk - 1) / chunk;
+  auto half = [&](size_t c) { return W->h_stage.as<uint64_t>() + (c & 1) * chunk; };
+  auto issue = [&](size_t c) -> cudaError_t {
+    const size_t lo = c * chunk, len = std::min(chunk, sw - lo);
+    cudaError_t e = cudaMemcpyAsync(half(c), W->stage.as<uint64_t>() + lo, 8 * len,
+                                    cudaMemcpyDeviceToHost, s);
+    return e == cudaSuccess ? cudaEventRecord(W->ev_stage[c & 1], s) : e;
+  };
   const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
-  const size_t n_thr = std::min<size_t>(std::min(16u, hw), 1 + total_words / (1u << 20));
-  if (n_thr <= 1) {
-    copy_range(0, total_words);
-  } else {
-    std::vector<std::thread> th;
-    const size_t per = (total_words + n_thr - 1) / n_thr;
-    for (size_t t = 0; t < n_thr; t++)
-      th.emplace_back(copy_range, t * per, std::min(total_words, (t + 1) * per));
-    for (auto &t : th) t.join();
+  double host_ms = 0;
+  if (n_chunks) CUDA_TRY(issue(0));
+  for (size_t c = 0; c < n_chunks; c++) {
+    // the half that chunk c + 1 fills held chunk c - 1, copied out in the last iteration
+    if (c + 1 < n_chunks) CUDA_TRY(issue(c + 1));
+    CUDA_TRY(cudaEventSynchronize(W->ev_stage[c & 1]));
+    const auto th0 = std::chrono::steady_clock::now();
+    const size_t lo = c * chunk, hi = std::min(sw, lo + chunk);
+    const uint64_t *src = half(c);
+    const size_t n_thr = std::min<size_t>(std::min(16u, hw), 1 + (hi - lo) / (1u << 20));
+    if (n_thr <= 1) {
+      copy_range(lo, hi, src, lo);
+    } else {
+      std::vector<std::thread> th;
+      const size_t per = (hi - lo + n_thr - 1) / n_thr;
+      for (size_t t = 0; t < n_thr; t++)
+        th.emplace_back(copy_range, lo + t * per, std::min(hi, lo + (t + 1) * per), src, lo);
+      for (auto &t : th) t.join();
+    }
+    host_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - th0)
+                   .count();
   }
+  CUDA_TRY(cudaStreamSynchronize(s));  // the device-side outputs too
+  t_stats.copy_out_ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - tc0).count();
+  t_stats.host_copy_ms = host_ms;
   return WPM_OK;
 }
 
@@ -1004,6 +1053,7 @@ static RunOptions options_from(const wpm_tuning *t, int mode) {
     o.ready_polls = t->ready_polls;
     o.idle_polls = t->idle_polls;
     o.test_unpublished = t->test_unpublished;
+    o.stage_chunk = t->stage_chunk_words;
   }
   return o;
 }

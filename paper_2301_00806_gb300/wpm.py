@@ -79,7 +79,7 @@ class Tuning(C.Structure):
                 ("donate_every", C.c_int32), ("graph", C.c_int32), ("engine", C.c_int32),
                 ("sweep_max_s", C.c_int32), ("ready_polls", C.c_int32),
                 ("idle_polls", C.c_int32), ("test_unpublished", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("stage_chunk_words", C.c_int32)]
 
 
 class RunStats(C.Structure):
@@ -88,7 +88,8 @@ class RunStats(C.Structure):
                 ("dfs_ms", C.c_double), ("expand_ms", C.c_double), ("search", C.c_int32),
                 ("size_class", C.c_int32), ("searches", C.c_int32), ("reserved", C.c_int32),
                 ("h2d_bytes", C.c_uint64), ("d2h_bytes", C.c_uint64),
-                ("graph_launches", C.c_uint64)]
+                ("graph_launches", C.c_uint64), ("run_ms", C.c_double),
+                ("copy_out_ms", C.c_double), ("host_copy_ms", C.c_double)]
 
 
 class EngineConfig(C.Structure):

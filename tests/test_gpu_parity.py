@@ -501,3 +501,20 @@ def test_n10_batch_default_is_per_thread_and_exact(W):
         for r, (s, c, nd, pr) in zip(res, rows):
             assert r.status == 0
             assert (r.count, r.nodes, r.probes) == (c, nd, pr), s
+
+
+@pytest.mark.parametrize("n_hi,chunk", [(4, 3), (6, 4099), (6, 100003)],
+                         ids=["n3_4_chunk3", "n3_6_chunk4099", "n3_6_chunk100003"])
+def test_host_lists_through_small_staging_chunks(W, n_hi, chunk):
+    """Host outputs leave the device chunk by chunk through two page-locked halves of a
+    staging buffer. Chunks much smaller than the lists (a list then spans many chunks, a
+    chunk holds parts of several lists, and with 3 words a mask can straddle two chunks) give
+    the oracle's sorted lists, counts, nodes and probes."""
+    insts = I.batch_duals(24, 3, n_hi, seed=7)
+    orc = [oracle_run(inst, cap=-2)[1] for inst in insts]
+    specs = [W.BatchSpec("dual", i.n, i.m, i.cols, cap=-2) for i in insts]
+    res = W.enumerate_batch(specs, list_mode=True, capacities=[o[0] + 1 for o in orc],
+                            tuning={"stage_chunk_words": chunk})
+    for g, o in zip(res, orc):
+        assert g.status == 0
+        assert_same(g, o)
