@@ -271,7 +271,8 @@ int wpm_enumerate_batch(const wpm_instance *inst, int count, wpm_output *outs, i
  * candidate tunings (search mode, i.e. one search per thread or per warp; breadth-first
  * frontier size; the hand-over chunk of per-thread searches: levels given and nodes between
  * hand-overs) on a sample of the batch, every k-th instance for about `sample` instances
- * (0: 256), in counting mode, and writes the fastest to *best. Counts do not depend on the
+ * (0: 256), in counting mode, each in two interleaved rounds keeping its best time, and
+ * writes the fastest to *best. Counts do not depend on the
  * tuning, so the candidates differ only in time. The choice is also kept, for the rest of
  * the process, under the batch's signature (the smallest and largest n, whether any map is
  * primal, and the number of maps rounded down to a power of two): wpm_enumerate_batch with
