@@ -368,7 +368,9 @@ typedef struct {
     int32_t slice_ms;       /* a step's search pass also ends this many milliseconds after it
                                began (every search parks at that time): it bounds how long a
                                queued job waits for admission, and passes that end together
-                               leave no tail; 0 = 100 ms, < 0 = the node budget alone      */
+                               leave no tail; 0 = by load (50 ms while fewer than half the
+                               searches parked work at the end of the last pass, else 100 ms),
+                               < 0 = the node budget alone                                  */
 } wpm_engine_config;
 
 /* Create an engine on the current device; stream may be NULL (the engine's own stream). */

@@ -148,7 +148,7 @@ struct wpm_engine {
   int k = 0, search = kSearchThread, tpb = 128, blocks = 0, n_searches = 0, max_depth = 0, iw = 0;
   int max_jobs = 0, max_n = 0;
   long long budget = 4096;
-  int slice_ms = 100;  // > 0: passes also end after this many milliseconds
+  int slice_ms = 0;  // > 0: passes also end after this many milliseconds; 0: by load; < 0: none
   size_t slot_bytes = 0;
   unsigned long long ring_cap = 0, dump_limit = 0, idle_limit = 1, hungry = 1;
   unsigned long long parked = 0;  // searches holding parked work after the last pass
@@ -332,6 +332,37 @@ int admit(wpm_engine *e) {
   CUDA_TRY(cudaMemcpyAsync(hq, e->q.p, sizeof(QueueCtl), cudaMemcpyDeviceToHost, e->s));
   CUDA_TRY(cudaStreamSynchronize(e->s));
   if (hq->err) return fail(WPM_ERR_NOMEM, "engine work ring overflow");
+  const unsigned long long roots_at = e->tail;
+  e->tail = hq->tail;
+
+  // One breadth-first level over the new roots: a new job enters its first pass as its root's
+  // children (up to M items, one per lowest facet), taken by as many searches at once, instead
+  // of as one item that spreads only as fast as searches hand work over. The roots' slots are
+  // marked empty. A root has at most M children, so the ring has room when this holds:
+  unsigned long long children = 0;
+  for (int sl : roots) children += (unsigned long long)e->slots[sl]->M + 1;
+  if (e->tail - e->head + children > e->ring_cap) return WPM_OK;  // left as roots
+  PassArgs pa;
+  memset(&pa, 0, sizeof(pa));
+  pa.inst = e->inst.as<InstDesc>();
+  pa.outs = e->outd.as<OutDesc>();
+  pa.ctr = e->ctr.as<unsigned long long>();
+  pa.ring = e->ring.as<uint32_t>();
+  pa.ring_cap = e->ring_cap;
+  pa.item_words = e->iw;
+  pa.q = e->q.as<QueueCtl>();
+  pa.max_depth = e->max_depth;
+  pa.clear_expanded = 1;
+  memset(hq, 0, sizeof(QueueCtl));
+  hq->head = e->head;
+  hq->tail = e->tail;
+  hq->limit = e->tail;
+  hq->head_start = roots_at;  // the items expanded: [roots_at, roots_at + roots)
+  CUDA_TRY(cudaMemcpyAsync(e->q.p, hq, sizeof(QueueCtl), cudaMemcpyHostToDevice, e->s));
+  CUDA_TRY(launch_expand(e->k, pa, (int)roots.size(), 256, e->s));
+  CUDA_TRY(cudaMemcpyAsync(hq, e->q.p, sizeof(QueueCtl), cudaMemcpyDeviceToHost, e->s));
+  CUDA_TRY(cudaStreamSynchronize(e->s));
+  if (hq->err) return fail(WPM_ERR_NOMEM, "engine work ring overflow");
   e->tail = hq->tail;
   return WPM_OK;
 }
@@ -353,7 +384,14 @@ int pass(wpm_engine *e) {
   pa.stack = e->stack.as<uint32_t>();
   pa.aff_scratch = e->aff.as<long long>();
   pa.budget = e->budget;
-  pa.time_left_ns = e->slice_ms > 0 ? (unsigned long long)e->slice_ms * 1000000ull : 0ull;
+  // the slice by load: when fewer than half the searches parked work at the end of the last
+  // pass the GPU has room, and 50 ms slices admit and retire jobs sooner; under load 100 ms
+  // slices park and resume the searches half as often (measured on the serving stream:
+  // 60 jobs/s p50 0.41 s with 50 ms, 0.49 s with 100 ms; 200 jobs/s 6.3e9 and 6.5e9 nodes/s)
+  const int slice = e->slice_ms > 0 ? e->slice_ms
+                    : e->slice_ms < 0 ? 0
+                                      : (2 * e->parked < (unsigned long long)e->n_searches ? 50 : 100);
+  pa.time_left_ns = (unsigned long long)slice * 1000000ull;
   pa.idle_limit = e->idle_limit;
   pa.dump_limit = e->dump_limit;
   {  // the row variant the resident jobs allow (m - n + 1 bounds a ridge's parents)
@@ -466,7 +504,7 @@ int wpm_engine_create(const wpm_engine_config *cfg, void *cuda_stream, wpm_engin
   e->max_jobs = cfg && cfg->max_jobs > 0 ? cfg->max_jobs : 1024;
   e->max_n = cfg && cfg->max_n > 0 ? std::min(cfg->max_n, 12) : 11;
   e->budget = cfg && cfg->budget > 0 ? cfg->budget : (1 << 20);
-  e->slice_ms = !cfg || cfg->slice_ms == 0 ? 100 : (cfg->slice_ms > 0 ? cfg->slice_ms : 0);
+  e->slice_ms = cfg ? cfg->slice_ms : 0;
   auto bail = [&](int code) {
     wpm_engine_destroy(e);
     return code;

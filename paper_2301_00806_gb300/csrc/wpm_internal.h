@@ -120,7 +120,8 @@ struct PassArgs {
   long long *aff_scratch;   // per-thread search: [n_threads * 2 * kMaxAffine]
   long long budget;         // nodes per search per pass (dfs)
   int trace;                // nonzero: count loop iterations and lane activity
-  int pad1;
+  int clear_expanded;       // breadth-first expansion: mark each expanded item's slot empty
+                            // (items behind it in the ring are still to be taken)
   unsigned long long idle_limit;  // once this many searches of a pass have stopped, the
                                   // others return their remaining work and stop too
   unsigned long long dump_limit;  // a search returns work to the ring only while fewer

@@ -702,7 +702,7 @@ __global__ void __maxnreg__(96) tdfs_kernel(PassArgs a) {
       base = 0;
       continue;
     }
-    // ---- every 64 nodes: end of the pass (budget, time, full ring), or hand-over
+    // ---- every 512 nodes: end of the pass (budget, time, full ring), or hand-over
     if (pass_nodes >= next_check) {
       next_check = pass_nodes + 512;
       const bool end = pass_nodes >= a.budget || vload(&q->full) || global_ns() >= t_end;

@@ -489,22 +489,25 @@ __global__ void __launch_bounds__(256) wexpand_kernel(PassArgs a, int n_items) {
   S.st = smem + wib * K::SMW;
   S.stk = nullptr;
   const unsigned long long idx = a.q->head_start + (unsigned long long)i;
-  const uint32_t *it = a.ring + (idx % a.ring_cap) * (unsigned long long)K::IW;
+  uint32_t *it = a.ring + (idx % a.ring_cap) * (unsigned long long)K::IW;
   if ((it[1] & 0xFFFFu) == kItemEmpty) return;
   S.bind(a.inst, a.outs, a.ctr, (int)it[0]);
   bool fresh;
-  if (!S.load(it, fresh)) {
+  if (S.load(it, fresh)) {
+    Entry e = S.resume(fresh);
+    while (S.next_child(e)) {
+      S.created(true);
+      S.write_item(a, kItemOpen, S.floor_, 0, 0, -1);  // unexpanded: its children are uncounted
+      S.retreat(e);
+    }
+  } else {
     S.probes++;
-    S.flush();
-    return;
-  }
-  Entry e = S.resume(fresh);
-  while (S.next_child(e)) {
-    S.created(true);
-    S.write_item(a, kItemOpen, S.floor_, 0, 0, -1);  // unexpanded: its children are uncounted
-    S.retreat(e);
   }
   S.flush();
+  if (a.clear_expanded) {  // every lane has read the item: its slot is now empty
+    __syncwarp();
+    if (S.lane == 0) it[1] = kItemEmpty;
+  }
 }
 
 // ------------------------------------------------------------------------------------
