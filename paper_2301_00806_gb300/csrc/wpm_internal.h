@@ -233,6 +233,12 @@ inline int rows_variant(int max_n, int max_parents) {
 cudaError_t launch_pass_prep(QueueCtl *q, int thread_mode, cudaStream_t s);
 cudaError_t launch_pass_check(QueueCtl *q, int thread_mode, cudaGraphConditionalHandle h,
                               unsigned long long max_passes, cudaStream_t s);
+// One-thread kernel after each level of a graph-driven breadth-first expansion: the level's
+// children become the next level's items, and h is set while another level is wanted.
+cudaError_t launch_expand_check(QueueCtl *q, cudaGraphConditionalHandle h,
+                                unsigned long long target, unsigned long long max_children,
+                                unsigned long long ring_cap, unsigned long long max_levels,
+                                cudaStream_t s);
 cudaError_t launch_setup(InstDesc *d_inst, int n_inst, cudaStream_t s);
 // The setup kernel over the instances d_inst[d_ids[0..n_ids)] only.
 cudaError_t launch_setup_ids(InstDesc *d_inst, const int32_t *d_ids, int n_ids, cudaStream_t s);
@@ -255,6 +261,9 @@ enum { kSearchThread = 1, kSearchWarp = 2 };
 
 // Breadth-first expansion: one warp per item; tpb a multiple of 32 (at most 256).
 cudaError_t launch_expand(int k, const PassArgs &a, int n_items, int tpb, cudaStream_t s);
+// The same over the queue's items [head_start, limit), read on the device, by the warps of a
+// grid of `blocks` blocks of 256 threads (a level of the graph-driven expansion loop).
+cudaError_t launch_expand_queued(int k, const PassArgs &a, int blocks, cudaStream_t s);
 // Depth-first pass in the given search mode (tpb 64, 128 or 256).
 cudaError_t launch_dfs(int k, int search, const PassArgs &a, int blocks, int tpb, cudaStream_t s);
 size_t dfs_smem_bytes(int k, int search, int tpb, int max_depth);

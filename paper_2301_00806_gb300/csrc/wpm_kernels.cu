@@ -315,6 +315,32 @@ __global__ void pass_check_kernel(QueueCtl *q, int thread_mode, cudaGraphConditi
   cudaGraphSetConditional(h, more ? 1u : 0u);
 }
 
+// After a level of the graph-driven expansion: its children, [limit, tail), are the next
+// level's items. Another level while no error was raised and the new level has items, fewer
+// than `target`, whose children fit in the ring (at most max_children each) -- the rule of the
+// host-driven loop -- and fewer than max_levels levels have run (a bound only: stopping early
+// leaves a smaller frontier, never a different result).
+__global__ void expand_check_kernel(QueueCtl *q, cudaGraphConditionalHandle h,
+                                    unsigned long long target, unsigned long long max_children,
+                                    unsigned long long ring_cap, unsigned long long max_levels) {
+  const unsigned long long live = q->tail - q->limit;
+  q->head_start = q->limit;
+  q->limit = q->tail;
+  q->head = q->tail;
+  q->passes++;
+  const bool more = q->err == 0 && live > 0 && live < target &&
+                    live * max_children + live <= ring_cap && q->passes < max_levels;
+  cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
+cudaError_t launch_expand_check(QueueCtl *q, cudaGraphConditionalHandle h,
+                                unsigned long long target, unsigned long long max_children,
+                                unsigned long long ring_cap, unsigned long long max_levels,
+                                cudaStream_t s) {
+  expand_check_kernel<<<1, 1, 0, s>>>(q, h, target, max_children, ring_cap, max_levels);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_pass_prep(QueueCtl *q, int thread_mode, cudaStream_t s) {
   pass_prep_kernel<<<1, 1, 0, s>>>(q, thread_mode);
   return cudaGetLastError();
@@ -390,6 +416,11 @@ cudaError_t launch_expand(int k, const PassArgs &a, int n_items, int tpb, cudaSt
   const int wpb = tpb / 32;
   const size_t smem = (size_t)wpb * state_words(k) * 4u;
   return dispatch(k, 0, a, (n_items + wpb - 1) / wpb, n_items, tpb, smem, s);
+}
+
+cudaError_t launch_expand_queued(int k, const PassArgs &a, int blocks, cudaStream_t s) {
+  const size_t smem = (size_t)8 * state_words(k) * 4u;
+  return dispatch(k, 0, a, blocks, -1, 256, smem, s);
 }
 
 cudaError_t launch_dfs(int k, int search, const PassArgs &a, int blocks, int tpb, cudaStream_t s) {

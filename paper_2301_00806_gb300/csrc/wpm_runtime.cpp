@@ -71,6 +71,24 @@ struct PassGraph {
   }
 };
 
+// The breadth-first expansion loop as an instantiated CUDA graph: a conditional while node
+// whose body is one level (the expansion over the queued items, then its check). Kept while
+// its arguments stay the same.
+struct ExpandGraph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  PassArgs pa;
+  int k = -1, blocks = 0;
+  unsigned long long target = 0, max_children = 0, ring_cap = 0, max_levels = 0;
+  void reset() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    exec = nullptr;
+    graph = nullptr;
+    k = -1;
+  }
+};
+
 struct Workspace {
   int device = -1;
   int sms = 0;
@@ -78,11 +96,13 @@ struct Workspace {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   cudaEvent_t ev_stage[2] = {nullptr, nullptr};  // the two halves of h_stage filled
   PassGraph pg;
+  ExpandGraph eg;
   DevBuf inst, outd, ctr, arena, cond, ids, q, ring, ready, stack, aff, park, out, seg, segs, stage,
       sweep, keep;
   PinBuf h_inst, h_outd, h_q, h_ctr, h_cond, h_ids, h_seg, h_segs, h_stage, h_sweep;
   void release() {
     pg.reset();
+    eg.reset();
     if (pg.capture) cudaStreamDestroy(pg.capture);
     pg.capture = nullptr;
     for (DevBuf *b : {&inst, &outd, &ctr, &arena, &cond, &ids, &q, &ring, &ready, &stack, &aff, &park, &out, &seg,
@@ -315,6 +335,82 @@ static cudaError_t launch_pass_graph(Workspace *W, const PassArgs &pa, int k, in
     G.search = search;
     G.blocks = blocks;
     G.tpb = tpb;
+  }
+  return cudaGraphLaunch(G.exec, s);
+}
+
+// Launch the breadth-first expansion loop as one graph (built on first use and kept while the
+// arguments stay the same). The queue holds the first level's items as [head_start, limit);
+// levels run until expand_check_kernel's rule stops them. cudaErrorNotSupported when this
+// CUDA has no conditional nodes (the caller then loops on the host).
+static cudaError_t launch_expand_graph(Workspace *W, const PassArgs &pa, int k, int blocks,
+                                       unsigned long long target,
+                                       unsigned long long max_children,
+                                       unsigned long long ring_cap,
+                                       unsigned long long max_levels, cudaStream_t s) {
+  ExpandGraph &G = W->eg;
+  if (W->pg.unsupported) return cudaErrorNotSupported;
+  const bool same = G.exec && G.k == k && G.blocks == blocks && G.target == target &&
+                    G.max_children == max_children && G.ring_cap == ring_cap &&
+                    G.max_levels == max_levels && memcmp(&G.pa, &pa, sizeof(PassArgs)) == 0;
+  if (!same) {
+    G.reset();
+    PassGraph &P = W->pg;  // its capture stream is shared
+    if (!P.capture) {
+      cudaError_t e = cudaStreamCreateWithFlags(&P.capture, cudaStreamNonBlocking);
+      if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = cudaGraphCreate(&G.graph, 0);
+    if (e != cudaSuccess) return e;
+    cudaGraphConditionalHandle h;
+    if (cudaGraphConditionalHandleCreate(&h, G.graph, 1, cudaGraphCondAssignDefault) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      G.reset();
+      return cudaErrorNotSupported;
+    }
+    alignas(cudaGraphNodeParams) unsigned char cp_bytes[sizeof(cudaGraphNodeParams)];
+    memset(cp_bytes, 0, sizeof(cp_bytes));
+    cudaGraphNodeParams &cp = *reinterpret_cast<cudaGraphNodeParams *>(cp_bytes);
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, G.graph, nullptr, nullptr, 0, &cp);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      G.reset();
+      return cudaErrorNotSupported;
+    }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(P.capture, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) {
+      G.reset();
+      return e;
+    }
+    cudaError_t e1 = launch_expand_queued(k, pa, blocks, P.capture);
+    cudaError_t e2 = launch_expand_check(pa.q, h, target, max_children, ring_cap, max_levels,
+                                         P.capture);
+    cudaGraph_t captured = nullptr;
+    e = cudaStreamEndCapture(P.capture, &captured);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e != cudaSuccess) {
+      G.reset();
+      return e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e);
+    }
+    e = cudaGraphInstantiate(&G.exec, G.graph, 0);
+    if (e != cudaSuccess) {
+      G.reset();
+      return e;
+    }
+    G.pa = pa;
+    G.k = k;
+    G.blocks = blocks;
+    G.target = target;
+    G.max_children = max_children;
+    G.ring_cap = ring_cap;
+    G.max_levels = max_levels;
   }
   return cudaGraphLaunch(G.exec, s);
 }
@@ -699,6 +795,44 @@ static int run(Workspace *W, std::vector<HostInst> &hi, const RunOptions &opt, c
     };
     timed_out = false;
     unsigned long long head = 0, tail = hq->tail;
+    {
+      // Without tracing the levels run on the device, as one graph launch: no host round
+      // trip per level (small maps take a dozen levels before their frontier is wide enough
+      // or their tree is done). The host loop below then finds nothing left to do.
+      const unsigned long long live = tail - head;
+      if (!trace && opt.graph >= 0 && live > 0 && (long long)live < frontier_target &&
+          live * (unsigned long long)max_children + live <= ring_cap) {
+        memset(hq, 0, sizeof(QueueCtl));
+        hq->head = tail;
+        hq->tail = tail;
+        hq->limit = tail;
+        hq->head_start = head;
+        CUDA_TRY(cudaMemcpyAsync(W->q.p, hq, sizeof(QueueCtl), cudaMemcpyHostToDevice, s));
+        count_copy(W->q.p, hq, sizeof(QueueCtl), cudaMemcpyHostToDevice);
+        if (timed) CUDA_TRY(cudaEventRecord(ev0, s));
+        const cudaError_t ge = launch_expand_graph(
+            W, pa, k, 4 * W->sms, (unsigned long long)frontier_target,
+            (unsigned long long)max_children, ring_cap, (unsigned long long)max_depth + 2, s);
+        if (ge == cudaSuccess) {
+          if (timed) CUDA_TRY(cudaEventRecord(ev1, s));
+          CUDA_TRY(cudaMemcpyAsync(hq, W->q.p, sizeof(QueueCtl), cudaMemcpyDeviceToHost, s));
+          count_copy(hq, W->q.p, sizeof(QueueCtl), cudaMemcpyDeviceToHost);
+          CUDA_TRY(cudaStreamSynchronize(s));
+          if (hq->err) return fail(WPM_ERR_NOMEM, "work ring overflow during expansion");
+          t_stats.expand_passes += hq->passes;
+          t_stats.kernel_launches += 2 * hq->passes;
+          if (timed) {
+            float ms = 0;
+            CUDA_TRY(cudaEventElapsedTime(&ms, ev0, ev1));
+            t_stats.expand_ms += ms;
+          }
+          head = hq->head_start;
+          tail = hq->tail;
+        } else if (ge != cudaErrorNotSupported) {
+          return fail(WPM_ERR_CUDA, "expansion graph: %s", cudaGetErrorString(ge));
+        }
+      }
+    }
     for (;;) {
       const unsigned long long live = tail - head;
       if (live == 0 || (long long)live >= frontier_target) break;

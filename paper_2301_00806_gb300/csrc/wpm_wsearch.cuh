@@ -478,35 +478,44 @@ struct WSearch {
 // Breadth-first expansion: each item's accepted children become items (one warp per item).
 // ------------------------------------------------------------------------------------
 
+// n_items >= 0: items [head_start, head_start + n_items), one warp each. n_items < 0: the
+// items [head_start, limit) of the queue, the warps of a fixed grid striding over them (a level
+// of the expansion loop that runs on the device).
 template <class K>
 __global__ void __launch_bounds__(256) wexpand_kernel(PassArgs a, int n_items) {
   extern __shared__ uint32_t smem[];
   const int wib = threadIdx.x >> 5;
-  const int i = blockIdx.x * (blockDim.x >> 5) + wib;
-  if (i >= n_items) return;  // whole warps leave together
+  const unsigned long long wpb = blockDim.x >> 5;
+  const unsigned long long n =
+      n_items >= 0 ? (unsigned long long)n_items : a.q->limit - a.q->head_start;
+  const unsigned long long stride = n_items >= 0 ? n : (unsigned long long)gridDim.x * wpb;
   WSearch<K> S;
   S.lane = threadIdx.x & 31;
   S.st = smem + wib * K::SMW;
   S.stk = nullptr;
-  const unsigned long long idx = a.q->head_start + (unsigned long long)i;
-  uint32_t *it = a.ring + (idx % a.ring_cap) * (unsigned long long)K::IW;
-  if ((it[1] & 0xFFFFu) == kItemEmpty) return;
-  S.bind(a.inst, a.outs, a.ctr, (int)it[0]);
-  bool fresh;
-  if (S.load(it, fresh)) {
-    Entry e = S.resume(fresh);
-    while (S.next_child(e)) {
-      S.created(true);
-      S.write_item(a, kItemOpen, S.floor_, 0, 0, -1);  // unexpanded: its children are uncounted
-      S.retreat(e);
+  // whole warps take an item or leave together
+  for (unsigned long long i = blockIdx.x * wpb + wib; i < n; i += stride) {
+    const unsigned long long idx = a.q->head_start + i;
+    uint32_t *it = a.ring + (idx % a.ring_cap) * (unsigned long long)K::IW;
+    if ((it[1] & 0xFFFFu) == kItemEmpty) continue;
+    S.bind(a.inst, a.outs, a.ctr, (int)it[0]);
+    bool fresh;
+    if (S.load(it, fresh)) {
+      Entry e = S.resume(fresh);
+      while (S.next_child(e)) {
+        S.created(true);
+        S.write_item(a, kItemOpen, S.floor_, 0, 0, -1);  // unexpanded: its children are uncounted
+        S.retreat(e);
+      }
+    } else {
+      S.probes++;
     }
-  } else {
-    S.probes++;
-  }
-  S.flush();
-  if (a.clear_expanded) {  // every lane has read the item: its slot is now empty
+    S.flush();
+    if (a.clear_expanded) {  // every lane has read the item: its slot is now empty
+      __syncwarp();
+      if (S.lane == 0) it[1] = kItemEmpty;
+    }
     __syncwarp();
-    if (S.lane == 0) it[1] = kItemEmpty;
   }
 }
 
