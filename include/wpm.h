@@ -170,9 +170,10 @@ typedef struct {
     int64_t hungry_items;
     int32_t donate_levels;
     int32_t donate_every;
-    int32_t graph;          /* 0: the depth-first pass loop runs as one CUDA graph launch (a
-                               conditional while node; not with a time limit or tracing);
-                               -1: the host launches each pass                             */
+    int32_t graph;          /* 0: the breadth-first levels and the depth-first pass loop each
+                               run as one CUDA graph launch (a conditional while node; the
+                               pass loop not with a time limit, neither with tracing);
+                               -1: the host launches each level and each pass             */
     int32_t engine;         /* 0: the canonical ridge-driven search. 1: the GF(2) cycle-space
                                sweep of Section 2.1 over its convenient basis: rows of forced
                                facets (and the base facet) fix coordinates of X as in Section
@@ -217,8 +218,9 @@ typedef struct {
     int32_t reserved;
     uint64_t h2d_bytes;        /* bytes copied host -> device by the run                       */
     uint64_t d2h_bytes;        /* bytes copied device -> host by the run                       */
-    uint64_t graph_launches;   /* CUDA graph launches (the depth-first pass loop run on the
-                                  device by a conditional while node)                          */
+    uint64_t graph_launches;   /* CUDA graph launches of the depth-first pass loop (run on the
+                                  device by a conditional while node; the breadth-first levels'
+                                  graph is counted in expand_passes alone)                     */
     double run_ms;             /* host time of the run, from the checked inputs to the results */
     double copy_out_ms;        /* host time of the copy-out: gather on the device, the copy to
                                   the page-locked staging buffer, the copies to host outputs   */
