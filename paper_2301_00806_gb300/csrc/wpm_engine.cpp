@@ -21,7 +21,6 @@
 #include <cstring>
 #include <deque>
 #include <map>
-#include <memory>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -84,7 +83,7 @@ struct Job {
 constexpr size_t kHostCacheBytes = 4ull << 30;
 
 struct HostCache {
-  std::map<size_t, std::vector<void *>> free;  // size class -> free blocks
+  std::map<size_t, std::vector<void *>> spare;  // size class -> blocks not in use
   std::map<void *, bool> locked;               // every block handed out or free: page-locked?
   size_t free_bytes = 0;
   static size_t size_class(size_t bytes) {
@@ -94,8 +93,8 @@ struct HostCache {
   }
   void *take(size_t bytes, size_t &cls) {
     cls = size_class(bytes);
-    auto it = free.find(cls);
-    if (it != free.end() && !it->second.empty()) {
+    auto it = spare.find(cls);
+    if (it != spare.end() && !it->second.empty()) {
       void *p = it->second.back();
       it->second.pop_back();
       free_bytes -= cls;
@@ -115,7 +114,7 @@ struct HostCache {
     auto it = locked.find(p);
     if (it == locked.end()) return;
     if (it->second) cudaFreeHost(p);
-    else ::free(p);
+    else free(p);
     locked.erase(it);
   }
   void give(void *p, size_t cls) {
@@ -124,14 +123,14 @@ struct HostCache {
       drop(p);
       return;
     }
-    free[cls].push_back(p);
+    spare[cls].push_back(p);
     free_bytes += cls;
   }
   void release_all() {
     std::vector<void *> all;
     for (auto &kv : locked) all.push_back(kv.first);
     for (void *p : all) drop(p);
-    free.clear();
+    spare.clear();
     free_bytes = 0;
   }
 };
