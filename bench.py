@@ -181,8 +181,8 @@ def algorithmic_ops(res, insts):
     return sum(3 * i.n * (r.nodes + r.probes) + 6 * i.n * r.nodes for r, i in zip(res, insts))
 
 
-def survey_ops(res, insts):
-    """The same work counted in 64-bit words as the plan of the path counts it: per node a
+def word_ops(res, insts):
+    """The same work counted in 64-bit words: per node a
     select over ceil(N/64) words, per tried child its n counter tests, per accepted child n
     counter updates and ceil(M/64) words of Out."""
     tot = 0
@@ -458,7 +458,7 @@ def run_ours(args, rank, world, oracle_res=None):
     dev_out = [dev_buf[int(offs[k]):int(offs[k + 1])] for k in range(len(specs))]
     nodes_step = sum(r.nodes for r in res)
     ops_step = algorithmic_ops(res, insts)
-    ops_step_survey = survey_ops(res, insts)
+    ops_step_words = word_ops(res, insts)
     # the roofline's peak: integer instructions per second of this GPU, measured (untimed)
     peak_ops, _ = wpm.int_peak(0)
     peak_popc, _ = wpm.int_peak(1)
@@ -576,8 +576,8 @@ def run_ours(args, rank, world, oracle_res=None):
                      "ops_model": "3n per tried child + 6n per accepted child (n ridge counters "
                                   "tested, then updated on entry and exit); frac uses this",
                      "ops_per_node": ops_step / nodes_step,
-                     "ops_per_node_word_count": ops_step_survey / nodes_step,
-                     "frac_word_count": (ops_step_survey * args.steps / (dfs_ms / 1000.0) /
+                     "ops_per_node_word_count": ops_step_words / nodes_step,
+                     "frac_word_count": (ops_step_words * args.steps / (dfs_ms / 1000.0) /
                                          peak_ops) if dfs_ms > 0 else None,
                      "peak_from": "measured: wpm_int_peak, independent lop3 + add chains on "
                                   "every SM (popc + xor chains: %.3g ops/s; nominal 152 x 128 "
