@@ -182,9 +182,9 @@ def algorithmic_ops(res, insts):
 
 
 def word_ops(res, insts):
-    """The same work counted in 64-bit words: per node a
-    select over ceil(N/64) words, per tried child its n counter tests, per accepted child n
-    counter updates and ceil(M/64) words of Out."""
+    """The same work counted in 64-bit words: per node a select over ceil(N/64) words, per
+    tried child its n counter tests, per accepted child n counter updates and ceil(M/64)
+    words of Out."""
     tot = 0
     for r, i in zip(res, insts):
         wn, wm = (r.N + 63) // 64, (r.M + 63) // 64
